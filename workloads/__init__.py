@@ -1,0 +1,126 @@
+"""Seeded synthetic inputs shared by the tests, the bench and the smoke check.
+
+This module holds none of the method's arithmetic: only geometry (a BCC tungsten
+supercell with a <111> dumbbell self-interstitial, the system of Sec. 3.1), seeded
+random draws (thermal displacements, Maxwell-Boltzmann velocities, random SNAP
+coefficients, uneven interval lengths) and the workload definitions.
+
+Recipe (stated again in the design doc):
+  * lattice: n x n x n conventional BCC cells, a = 3.1652 Angstrom, periodic box n*a;
+  * SIA: the atom at the site nearest the box centre is replaced by two atoms at
+    s +- 1.1 Angstrom * (1,1,1)/sqrt(3)  (2 n^3 + 1 atoms);
+  * displacements: i.i.d. N(0, sigma^2) per coordinate (sigma = 0.05 Angstrom);
+  * velocities: i.i.d. N(0, k_B T / m) per coordinate, centre-of-mass velocity removed;
+  * SNAP coefficients: beta_0 = -8.9 eV, beta_t ~ N(0, 0.01^2);
+  * interval lengths: L_b ~ U{100, ..., 2000}.
+Every draw comes from numpy's PCG64 seeded by a SplitMix64-derived sub-seed of one
+master seed, so each stream is reproducible on its own.
+"""
+import numpy as np
+
+A_W = 3.1652             # BCC tungsten lattice constant, Angstrom
+M_W = 183.84             # u
+KB = 8.617333262e-5      # eV/K
+FTOA = 9648.533215665    # eV/(Angstrom u) -> Angstrom/ps^2
+
+SNAP = dict(twojmax=8, rcut=4.73, rfac0=0.99363, rmin0=0.0, switchflag=1)
+FS_W = dict(d=4.400224, A=1.896373, c=3.25, c0=47.1346499, c1=-33.7665655, c2=6.2541999)
+BETA0 = -8.9
+
+
+def splitmix64(x: int) -> int:
+    """One SplitMix64 output for state x (used only to derive independent sub-seeds)."""
+    z = (x + 0x9E3779B97F4A7C15) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & 0xFFFFFFFFFFFFFFFF
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & 0xFFFFFFFFFFFFFFFF
+    return z ^ (z >> 31)
+
+
+def subseed(master: int, stream: int) -> int:
+    return splitmix64((master * 0x100000001B3 + stream) & 0xFFFFFFFFFFFFFFFF)
+
+
+def rng(master: int, stream: int) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64(subseed(master, stream)))
+
+
+def bcc(ncell: int, a: float = A_W):
+    """Perfect BCC positions [3, 2 ncell^3] and the orthorhombic box [3]."""
+    g = np.arange(ncell, dtype=np.float64)
+    cx, cy, cz = np.meshgrid(g, g, g, indexing="ij")
+    corner = np.stack([cx.ravel(), cy.ravel(), cz.ravel()])
+    pos = np.concatenate([corner, corner + 0.5], axis=1) * a
+    box = np.full(3, ncell * a)
+    return np.ascontiguousarray(pos), box
+
+
+def bcc_sia(ncell: int, a: float = A_W, split: float = 1.1):
+    """BCC supercell with one <111> dumbbell interstitial: [3, 2 ncell^3 + 1] and box."""
+    pos, box = bcc(ncell, a)
+    centre = box / 2
+    s = int(np.argmin(np.sum((pos - centre[:, None]) ** 2, axis=0)))
+    site = pos[:, s].copy()
+    u = np.ones(3) / np.sqrt(3.0)
+    rest = np.delete(pos, s, axis=1)
+    out = np.concatenate([rest, (site + split * u)[:, None], (site - split * u)[:, None]], axis=1)
+    return np.ascontiguousarray(out), box
+
+
+def displaced(pos, sigma, gen: np.random.Generator, count=None):
+    """count copies (or one if None) of pos with i.i.d. Gaussian displacements."""
+    if count is None:
+        return np.ascontiguousarray(pos + gen.normal(0.0, sigma, size=pos.shape))
+    return np.ascontiguousarray(pos[None] + gen.normal(0.0, sigma, size=(count,) + pos.shape))
+
+
+def velocities(natoms, T, gen: np.random.Generator, count=None, mass=M_W):
+    """Maxwell-Boltzmann velocities in Angstrom/ps, centre-of-mass motion removed."""
+    s = np.sqrt(KB * T / mass * FTOA)
+    shape = (3, natoms) if count is None else (count, 3, natoms)
+    v = gen.normal(0.0, s, size=shape)
+    v -= v.mean(axis=-1, keepdims=True)
+    return np.ascontiguousarray(v)
+
+
+def snap_beta(nB, gen: np.random.Generator, std=0.01, beta0=BETA0):
+    b = np.empty(1 + nB)
+    b[0] = beta0
+    b[1:] = gen.normal(0.0, std, size=nB)
+    return b
+
+
+def n_bispectrum(twojmax: int) -> int:
+    """Number of triples j2 <= j1 <= j <= J/2 with j <= j1 + j2 and integer j1+j2+j."""
+    c = 0
+    for tj1 in range(twojmax + 1):
+        for tj2 in range(tj1 + 1):
+            for tj in range(tj1, twojmax + 1):
+                if tj <= tj1 + tj2 and (tj1 + tj2 + tj) % 2 == 0:
+                    c += 1
+    return c
+
+
+def interval_lengths(count, gen: np.random.Generator, lo=100, hi=2000):
+    return gen.integers(lo, hi + 1, size=count).astype(np.int32)
+
+
+# ---- the workloads ------------------------------------------------------------------
+
+def small_system(master=2212, nconf=16, sigma=0.05, twojmax=8):
+    """129 atoms (4^3 cells + SIA), nconf displaced copies, random beta."""
+    pos, box = bcc_sia(4)
+    P = displaced(pos, sigma, rng(master, 1), count=nconf)
+    beta = snap_beta(n_bispectrum(twojmax), rng(master, 2))
+    return P, box, beta
+
+
+def batch_workload(master=2212, nbatch=64, T=1500.0, lo=100, hi=2000, ncell=4, sigma=0.05, twojmax=8):
+    """nbatch members of the (ncell^3 + SIA) system with uneven lengths L_b ~ U{lo..hi}."""
+    pos, box = bcc_sia(ncell)
+    n = pos.shape[1]
+    q = displaced(pos, sigma, rng(master, 11), count=nbatch)
+    v = velocities(n, T, rng(master, 12), count=nbatch)
+    beta = snap_beta(n_bispectrum(twojmax), rng(master, 2))
+    L = interval_lengths(nbatch, rng(master, 13), lo, hi)
+    ids = np.arange(nbatch, dtype=np.int64)
+    return q, v, box, beta, L, ids
