@@ -94,7 +94,8 @@ def adaptive(q0, p0, N, delta_conv, delta_expl, F, C, metric="rel", max_iter=100
     """Algorithm 2.  Returns (cur, log) with cur a dict n -> (q, p) for 0 <= n <= N.
 
     ``trace`` (optional list) receives one tuple per parareal iteration:
-    (N_init, N_final before the sweep, delta, N_final after the sweep)."""
+    (N_init, N_final before the sweep, delta, n at which the sweep stopped (N_final if it
+    completed), N_final after the sweep)."""
     N_init, N_final = 0, 0
     delta = (delta_conv + delta_expl) / 2
     cur = {0: (np.array(q0, dtype=np.float64), np.array(p0, dtype=np.float64))}
@@ -117,14 +118,16 @@ def adaptive(q0, p0, N, delta_conv, delta_expl, F, C, metric="rel", max_iter=100
             J = {n: _sub(f, c) for n, f, c in zip(ns, fine, coarse)}
             log.windows[-1]["subs"][-1][1] += 1                    # k^{N_slab}_conv += 1
             n_fin_before = N_final
+            n_stop = N_final
             for n in range(N_init, N_final):
                 cur[n + 1] = _add(C([cur[n]], [n])[0], J[n])
                 delta = window_error(prev, cur, N_init, n + 1, metric)
                 if delta > delta_expl:
+                    n_stop = n
                     N_final = max(n, N_init + 1)                   # N_final := n (clamped)
                     break
             if trace is not None:
-                trace.append((N_init, n_fin_before, delta, N_final))
+                trace.append((N_init, n_fin_before, delta, n_stop, N_final))
             iters += 1
             if iters > max_iter:
                 raise RuntimeError("adaptive parareal did not terminate")

@@ -1,0 +1,111 @@
+// Finnis-Sinclair EAM on one system per CTA (coarse potential, Sec. 3.1):
+//   rho_i = sum_{j != i, r < d} (r - d)^2,
+//   E = sum_i -A sqrt(rho_i) + 1/2 sum_{i != j, r < c} (r - c)^2 (c0 + c1 r + c2 r^2),
+//   F_i = sum_j [ (F'(rho_i) + F'(rho_j)) 2 (r - d) [r<d] + phi'(r) [r<c] ] (r_j - r_i) / r,
+//   F'(rho) = -A / (2 sqrt rho), 0 when rho = 0.
+// Positions live in shared memory (FP64 rows plus a wrapped FP32 copy used to screen pairs).
+// FP64 mode evaluates every pair term in FP64 from the exact minimum-image displacement;
+// FP32_BULK evaluates pair terms in FP32 and sums in FP64.
+#pragma once
+
+#include "device_common.cuh"
+#include "snap_device.cuh"   // disp64 / r2_64
+
+namespace pmd {
+
+struct FSDev {
+    double d, A, c, c0, c1, c2;
+    float screen2;   // (max(d, c) + margin)^2 for the FP32 screen
+};
+
+struct EamShared {
+    double* q;    // [3][n]
+    float4* qf;   // [n] wrapped to [0, L)
+    double* F;    // [3][n]
+    double* dF;   // [n]
+};
+
+__device__ __forceinline__ float4 wrap_f32(double x, double y, double z, const double box[3]) {
+    x -= box[0] * floor(x / box[0]);
+    y -= box[1] * floor(y / box[1]);
+    z -= box[2] * floor(z / box[2]);
+    return make_float4((float)x, (float)y, (float)z, 0.f);
+}
+
+__device__ __forceinline__ bool screen_pair(const float4& a, const float4& b, const float boxf[3], float s2) {
+    float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+    dx -= boxf[0] * rintf(dx / boxf[0]);
+    dy -= boxf[1] * rintf(dy / boxf[1]);
+    dz -= boxf[2] * rintf(dz / boxf[2]);
+    return dx * dx + dy * dy + dz * dz < s2;
+}
+
+// exact pair geometry in the chosen precision: returns r and the displacement r_j - r_i
+template <typename real>
+__device__ __forceinline__ real pair_geom(const EamShared& s, int n, int i, int j, const double box[3],
+                                          const float boxf[3], real d[3]) {
+    if constexpr (sizeof(real) == 8) {
+        double dd[3];
+        disp64(s.q, n, i, j, box, dd);
+        d[0] = dd[0];
+        d[1] = dd[1];
+        d[2] = dd[2];
+        return sqrt(r2_64(dd));
+    } else {
+        const float4 a = s.qf[i], b = s.qf[j];
+        float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
+        dx -= boxf[0] * rintf(dx / boxf[0]);
+        dy -= boxf[1] * rintf(dy / boxf[1]);
+        dz -= boxf[2] * rintf(dz / boxf[2]);
+        d[0] = dx;
+        d[1] = dy;
+        d[2] = dz;
+        return sqrtf(dx * dx + dy * dy + dz * dz);
+    }
+}
+
+// Forces into s.F (and per-atom energies into Eat if non-null).  All threads of the CTA call
+// it; it ends with __syncthreads().
+template <typename real>
+__device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], const FSDev& p, double* Eat) {
+    const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
+    const real d_ = (real)p.d, c_ = (real)p.c, c0 = (real)p.c0, c1 = (real)p.c1, c2 = (real)p.c2;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 qi = s.qf[i];
+        double rho = 0.0, ep = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i || !screen_pair(qi, s.qf[j], boxf, p.screen2)) continue;
+            real dv[3];
+            const real r = pair_geom<real>(s, n, i, j, box, boxf, dv);
+            if (r < d_) rho += (double)((r - d_) * (r - d_));
+            if (r < c_) ep += 0.5 * (double)((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
+        }
+        s.dF[i] = rho > 0.0 ? -p.A / (2.0 * sqrt(rho)) : 0.0;
+        if (Eat) Eat[i] = ep - p.A * sqrt(rho);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 qi = s.qf[i];
+        const double dFi = s.dF[i];
+        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i || !screen_pair(qi, s.qf[j], boxf, p.screen2)) continue;
+            real dv[3];
+            const real r = pair_geom<real>(s, n, i, j, box, boxf, dv);
+            real dEdr = real(0);
+            if (r < d_) dEdr += (real)(dFi + s.dF[j]) * real(2) * (r - d_);
+            if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
+            if (r < d_ || r < c_) {
+                f0 += (double)(dEdr * dv[0] / r);
+                f1 += (double)(dEdr * dv[1] / r);
+                f2 += (double)(dEdr * dv[2] / r);
+            }
+        }
+        s.F[i] = f0;
+        s.F[n + i] = f1;
+        s.F[2 * n + i] = f2;
+    }
+    __syncthreads();
+}
+
+}  // namespace pmd

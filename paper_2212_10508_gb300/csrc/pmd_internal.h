@@ -1,0 +1,100 @@
+// Internal declarations of the pmd library (host side): contexts, tables, error helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/pmd.h"
+#include "status_bits.h"
+
+namespace pmd {
+
+// ---- errors ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define PMD_CUDA_TRY(call)                                         \
+    do {                                                           \
+        cudaError_t _e = (call);                                   \
+        if (_e != cudaSuccess) return ::pmd::cuda_fail(_e, #call); \
+    } while (0)
+
+int status_to_code(int bits);
+
+// ---- device buffers --------------------------------------------------------------------
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t need);   // grow (never shrinks); returns PMD_OK or an error code
+    void release();
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ---- SNAP tables -----------------------------------------------------------------------
+// Half layout of U and Y: for each level tj (= 2j), rows p = 0..tj (p = j + m'),
+// columns q = qlo(tj)..tj (q = j + m, m >= 0), qlo = (tj + 1) / 2, row-major.
+// Full layout: rows p = 0..tj, columns q = 0..tj, row-major, levels concatenated.
+inline int qlo(int tj) { return (tj + 1) / 2; }
+inline int ncol_half(int tj) { return tj + 1 - qlo(tj); }
+inline int uoff_full(int tj) { return tj * (tj + 1) * (2 * tj + 1) / 6; }
+
+struct SnapHostTables {
+    int twojmax = 0;
+    int nB = 0;                       // bispectrum components
+    int nhalf = 0, nfull = 0;         // element counts of the half and full layouts
+    std::vector<int> tri;             // [nB][3] (2j1, 2j2, 2j), j2 <= j1 <= j
+    // U half elements: recursion and force-pass metadata
+    std::vector<int> hoff;            // [twojmax+2] offsets of each level in the half layout
+    // contraction blocks (ta >= tb, tj): Z^j_{ab} feeds Y^j with coefficient beta_eff(block)
+    std::vector<int> blk_ta, blk_tb, blk_tj, blk_cgoff;
+    std::vector<double> cg;           // per block [(ta+1)][(tb+1)]: <a m1 b m2 | J m1+m2>
+    std::vector<int> beff_ptr;        // CSR over blocks: contributions (t, coef)
+    std::vector<int> beff_t;
+    std::vector<double> beff_c;
+    // Y jobs: per lane a contiguous list, packed int4 {e | blk<<16, tj|p<<8|q<<16|s<<24, ta|tb<<8, cgoff}
+    std::vector<int> jobs;            // [njobs][4]
+    int lane_begin[33];
+    double total_terms = 0;           // CG terms per atom (for the flop model)
+    // bispectrum jobs (energy path): per triple t the block id of (j1, j2, j)
+    std::vector<int> tri_blk;
+};
+int build_snap_tables(int twojmax, SnapHostTables* T);
+
+}  // namespace pmd
+
+// ---- contexts -------------------------------------------------------------------------
+struct pmd_snap {
+    pmd_snap_params p;
+    pmd::SnapHostTables T;
+    int device = 0;
+    // device copies of the tables
+    pmd::DevBuf d_elem;      // packed per-half-element records (precision dependent)
+    pmd::DevBuf d_cg;        // CG values (precision dependent)
+    pmd::DevBuf d_blk;       // int4 per block {ta, tb, tj, cgoff}
+    pmd::DevBuf d_beffptr, d_befft, d_beffc;
+    pmd::DevBuf d_jobs;      // int4 jobs
+    pmd::DevBuf d_lanebeg;   // int[33]
+    pmd::DevBuf d_triblk;    // int4 per triple {blk, ta, tb, tj}
+    // scratch
+    pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_utot, s_B, s_status;
+    int cap_atoms = 0;
+    size_t elem_bytes = 0;   // bytes of one element record
+};
+
+struct pmd_engine {
+    pmd_engine_params p;
+    pmd_snap* snap = nullptr;        // owned
+    pmd::DevBuf beta;                // [1+nB] FP64
+    pmd::DevBuf status;              // int status word + barrier words
+    pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_vh, s_order, s_Ls, s_result;
+    int cap_batch = 0;
+    int device = 0;
+    int num_sms = 0;
+    void* pinned = nullptr;          // small pinned host buffer for parareal_correct results
+};
+
+struct pmd_adaptive;  // defined in adaptive.cpp

@@ -1,0 +1,655 @@
+// Batched propagation of parareal intervals and the parareal correction sweep.
+//
+//  * FINE (SNAP): one persistent cooperative kernel runs every member's sub-steps.  Members
+//    are sorted by their number of steps (longest first) so that the members still active at
+//    sub-step l form a prefix; each sub-step is two grid-wide phases separated by bounded
+//    grid barriers: (A) one warp per active atom builds its neighbour list and its pair
+//    derivatives dE_i/dr_ik, (B) one thread per active atom gathers its force and advances
+//    the Langevin scheme.  Uneven interval lengths cost nothing beyond the active prefix.
+//  * COARSE (EAM): one CTA per member runs the whole interval in shared memory.
+//  * parareal_correct: one CTA walks the window sequentially (Algorithm 2's inner loop) with
+//    the same per-CTA coarse code, so C(cur_n) here equals C(prev_n) of the batched path bit
+//    for bit when the states are equal.
+#include <algorithm>
+
+#include "eam_device.cuh"
+#include "langevin_device.cuh"
+#include "pmd_internal.h"
+#include "snap_kernels.cuh"
+
+namespace pmd {
+
+SnapView snap_view(const pmd_snap* s, const double* beta);
+int snap_reserve_impl(pmd_snap* s, long na);
+
+#ifndef FINE_THREADS
+#define FINE_THREADS 256
+#endif
+constexpr int COARSE_MAX_THREADS = 512;   // 90 registers per thread: 512 fit the register file
+
+// ---- host-side parameter packing -----------------------------------------------------------
+LangevinDev make_langevin(const pmd_langevin& lp) {
+    LangevinDev L{};
+    const double kT_m = KB * lp.T / lp.mass * FTOA;
+    const double f2a = FTOA / lp.mass;
+    L.dt = lp.dt;
+    L.hdt = 0.5 * lp.dt;
+    L.hdf = 0.5 * lp.dt * f2a;
+    L.hdg = 0.5 * lp.dt * lp.gamma;
+    for (int C = 0; C < 4; ++C) L.sig[C] = 0.5 * std::sqrt(2.0 * lp.gamma * kT_m * (double)C * lp.dt);
+    L.c1 = std::exp(-lp.gamma * lp.dt);
+    L.c2 = std::sqrt(kT_m * (1.0 - L.c1 * L.c1));
+    L.scheme = lp.scheme;
+    L.schedule = lp.schedule;
+    L.seed = lp.seed;
+    return L;
+}
+
+FSDev make_fs(const pmd_fs_params& p) {
+    FSDev f{p.d, p.A, p.c, p.c0, p.c1, p.c2, 0.f};
+    const double rm = std::max(p.d, p.c) + 1e-3;
+    f.screen2 = (float)(rm * rm);
+    return f;
+}
+
+// ---- FINE: persistent cooperative kernel ---------------------------------------------------
+struct FineArgs {
+    SnapView v;
+    int nbatch, n;
+    double box0, box1, box2;
+    double* q;
+    double* vel;
+    long stride;
+    const int32_t* nsteps;
+    const int64_t* ids;
+    LangevinDev L;
+    // scratch
+    int* nbr;
+    int* nnb;
+    void* dedr;
+    float4* qf;
+    double* vh;
+    const int* order;     // members sorted by nsteps, longest first
+    const int* Ls;        // nsteps in that order
+    const int* Lmax;
+    unsigned int* bar;
+    int* status;
+};
+
+__global__ void k_fine_prologue(const int32_t* __restrict__ nsteps, int nbatch, int schedule, int* __restrict__ order,
+                                int* __restrict__ Ls, int* __restrict__ Lmax, int* status) {
+    __shared__ int s_max;
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    for (int b = threadIdx.x; b < nbatch; b += blockDim.x) {
+        int Lb = nsteps[b];
+        if (Lb < 0 || (schedule == PMD_SCHED_L1_SYM && Lb > 1)) {
+            flag(status, ST_BADARG);
+            Lb = 0;
+        }
+        int rank = 0;
+        for (int c = 0; c < nbatch; ++c) {
+            int Lc = nsteps[c];
+            if (Lc < 0 || (schedule == PMD_SCHED_L1_SYM && Lc > 1)) Lc = 0;
+            rank += (Lc > Lb) || (Lc == Lb && c < b);
+        }
+        order[rank] = b;
+        Ls[rank] = Lb;
+        atomicMax(&s_max, Lb);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *Lmax = s_max;
+}
+
+__global__ void k_wrap_members(const double* __restrict__ q, long stride, int nbatch, int n, double b0, double b1,
+                               double b2, float4* __restrict__ qf) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nbatch * n) return;
+    const long m = idx / n;
+    const int i = (int)(idx % n);
+    const double* Q = q + m * stride;
+    const double box[3] = {b0, b1, b2};
+    qf[idx] = wrap_f32(Q[i], Q[n + i], Q[2 * n + i], box);
+}
+
+// number of members with at least max(ell, 1) steps (Ls sorted descending)
+__device__ __forceinline__ int active_members(const int* Ls, int nbatch, int ell) {
+    const int need = ell < 1 ? 1 : ell;
+    int lo = 0, hi = nbatch;   // first index with Ls < need
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (Ls[mid] >= need) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename real>
+__device__ __forceinline__ void fine_phase_b(const FineArgs& a, int m, int k, int ell) {
+    const int n = a.n;
+    const int L = a.nsteps[m] < 0 ? 0 : a.nsteps[m];
+    double F[3];
+    gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n, (const real*)a.dedr + (long)m * n * NMAX * 3, k,
+                       F, a.status);
+    double* Q = a.q + m * a.stride;
+    double* V = a.vel + m * a.stride;
+    double* VH = a.vh + (long)m * 3 * n;
+    const LangevinDev& Lp = a.L;
+    const double box[3] = {a.box0, a.box1, a.box2};
+    double G[3];
+    const int64_t nid = a.ids[m];
+    bool bad = false;
+    if (Lp.scheme == PMD_SCHEME_PAPER) {
+        normals3(Lp.seed, nid, ell, k, G);
+        const double s = sched_sigma(Lp, ell);
+#pragma unroll
+        for (int al = 0; al < 3; ++al) {
+            const long e = (long)al * n + k;
+            double v = V[e];
+            double vh = ell == 0 ? v : VH[e];
+            if (ell > 0) v = half_kick(Lp, vh, F[al], vh, s, G[al]);           // finish step ell-1
+            if (ell < L) {
+                double vhn = half_kick(Lp, v, F[al], vh, s, G[al]);            // first half of step ell
+                double qn = drift(Q[e], Lp.dt, vhn);
+                if (!isfinite(qn)) bad = true;
+                if (fabs(qn - Q[e]) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
+                Q[e] = qn;
+                VH[e] = vhn;
+            }
+            V[e] = v;
+        }
+    } else {
+        if (ell < L) normals3(Lp.seed, nid, ell, k, G);
+#pragma unroll
+        for (int al = 0; al < 3; ++al) {
+            const long e = (long)al * n + k;
+            double v = V[e];
+            if (ell > 0) v = kick_b(Lp, v, F[al]);
+            if (ell < L) {
+                double q = Q[e];
+                const double q0 = q;
+                v = kick_b(Lp, v, F[al]);
+                q = __dadd_rn(q, __dmul_rn(Lp.hdt, v));
+                v = ou_o(Lp, v, G[al]);
+                q = __dadd_rn(q, __dmul_rn(Lp.hdt, v));
+                if (!isfinite(q)) bad = true;
+                if (fabs(q - q0) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
+                Q[e] = q;
+            }
+            V[e] = v;
+        }
+    }
+    if (bad) flag(a.status, ST_NONFINITE);
+    if (ell < L && sizeof(real) == 4) a.qf[(long)m * n + k] = wrap_f32(Q[k], Q[n + k], Q[2 * n + k], box);
+}
+
+template <typename real, int TJ>
+__global__ void __launch_bounds__(FINE_THREADS) k_fine_persistent(FineArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, a.v);
+    snap_shared_load<real, TJ>(sh, a.v);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long gwarp = (long)blockIdx.x * wpb + warp, nwarps = (long)gridDim.x * wpb;
+    const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (long)gridDim.x * blockDim.x;
+    const int n = a.n;
+    const double box[3] = {a.box0, a.box1, a.box2};
+    const GridBarrier gb{a.bar, gridDim.x};
+    const int Lmax = *a.Lmax;
+    for (int ell = 0; ell <= Lmax; ++ell) {
+        const int A = active_members(a.Ls, a.nbatch, ell);
+        if (A == 0) break;
+        const long items = (long)A * n;
+        for (long it = gwarp; it < items; it += nwarps) {
+            const int m = a.order[it / n];
+            const int i = (int)(it % n);
+            real* dd = (real*)a.dedr + ((long)m * n + i) * NMAX * 3;
+            snap_atom_warp<real, TJ>(sh.ws[warp], sh.elem, a.v.jobs, sh.lane_begin, sh.cg, sh.beff, a.v.sp, lane, n,
+                                     i, a.q + m * a.stride, a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX,
+                                     a.nnb + (long)m * n + i, dd, nullptr, a.status);
+        }
+        if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
+        for (long it = gtid; it < items; it += nthreads) {
+            const int m = a.order[it / n];
+            const int k = (int)(it % n);
+            fine_phase_b<real>(a, m, k, ell);
+        }
+        if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
+    }
+}
+
+template <typename real, int TJ>
+static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, long stride, const int32_t* nsteps,
+                       const int64_t* ids, const pmd_langevin& lp, cudaStream_t st) {
+    pmd_snap* s = e->snap;
+    FineArgs a{};
+    a.v = snap_view(s, e->beta.as<double>());
+    a.nbatch = nbatch;
+    a.n = n;
+    a.box0 = e->p.box[0];
+    a.box1 = e->p.box[1];
+    a.box2 = e->p.box[2];
+    a.q = q;
+    a.vel = v;
+    a.stride = stride;
+    a.nsteps = nsteps;
+    a.ids = ids;
+    a.L = make_langevin(lp);
+    a.nbr = e->s_nbr.as<int>();
+    a.nnb = e->s_nnb.as<int>();
+    a.dedr = e->s_dedr.p;
+    a.qf = e->s_qf.as<float4>();
+    a.vh = e->s_vh.as<double>();
+    a.order = e->s_order.as<int>();
+    a.Ls = e->s_order.as<int>() + e->cap_batch;
+    a.Lmax = e->s_order.as<int>() + 2 * e->cap_batch;
+    unsigned int* words = reinterpret_cast<unsigned int*>(e->status.as<int>() + 1);
+    a.bar = words;
+    a.status = e->status.as<int>();
+    PMD_CUDA_TRY(cudaMemsetAsync(words, 0, 4 * sizeof(unsigned int), st));
+    k_fine_prologue<<<1, 1024, 0, st>>>(nsteps, nbatch, lp.schedule, e->s_order.as<int>(), (int*)a.Ls, (int*)a.Lmax,
+                                        a.status);
+    PMD_CUDA_TRY(cudaGetLastError());
+    if (sizeof(real) == 4) {
+        const long na = (long)nbatch * n;
+        k_wrap_members<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(q, stride, nbatch, n, a.box0, a.box1, a.box2,
+                                                                     a.qf);
+        PMD_CUDA_TRY(cudaGetLastError());
+    }
+    const size_t sm = snap_shared_bytes<real, TJ>(a.v, FINE_THREADS / 32);
+    auto kern = k_fine_persistent<real, TJ>;
+    PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int per_sm = 0;
+    PMD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FINE_THREADS, sm));
+    if (per_sm < 1) return fail(PMD_EUNSUPPORTED, "persistent SNAP kernel does not fit on an SM");
+    const int grid = per_sm * e->num_sms;
+    void* args[] = {&a};
+    PMD_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(FINE_THREADS), args, sm, st));
+    return PMD_OK;
+}
+
+int fine_propagate(pmd_engine* e, int nbatch, int n, double* q, double* v, long stride, const int32_t* nsteps,
+                   const int64_t* ids, const pmd_langevin& lp, cudaStream_t st) {
+    const bool f64 = e->p.fine.precision == PMD_FP64;
+    switch (e->p.fine.twojmax) {
+#define PMD_FINE_CASE(TJV)                                                                         \
+    case TJV:                                                                                      \
+        return f64 ? launch_fine<double, TJV>(e, nbatch, n, q, v, stride, nsteps, ids, lp, st)     \
+                   : launch_fine<float, TJV>(e, nbatch, n, q, v, stride, nsteps, ids, lp, st);
+        PMD_FINE_CASE(2)
+        PMD_FINE_CASE(4)
+        PMD_FINE_CASE(6)
+        PMD_FINE_CASE(8)
+#undef PMD_FINE_CASE
+    }
+    return fail(PMD_EUNSUPPORTED, "twojmax must be 2, 4, 6 or 8");
+}
+
+// ---- COARSE: one CTA per interval ----------------------------------------------------------
+// Shared memory: q [3][n] FP64, qf [n], F [3][n], dF [n].  Velocities v and v_{l-1/2} of the
+// thread's own atoms (i = tid + k*blockDim) stay in registers.
+template <int KMAX>
+struct OwnState {
+    double v[KMAX][3];
+    double vh[KMAX][3];
+};
+
+__host__ __device__ inline size_t coarse_smem_bytes(int n) {
+    return (size_t)n * (3 * 8 + 16 + 3 * 8 + 8) + 64;
+}
+
+__device__ inline EamShared coarse_carve(unsigned char* smem, int n) {
+    EamShared s;
+    s.q = reinterpret_cast<double*>(smem);
+    s.F = s.q + 3 * n;
+    s.dF = s.F + 3 * n;
+    s.qf = reinterpret_cast<float4*>(align_up(reinterpret_cast<size_t>(s.dF + n), 16));
+    return s;
+}
+
+// Runs nsteps sub-steps of interval nid on the CTA-resident state (positions in s.q/s.qf,
+// velocities in own.v).  All threads call it.
+template <typename real, int KMAX>
+__device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int n, const double box[3],
+                                    const FSDev& fs, const LangevinDev& L, int nsteps, int64_t nid, int* status) {
+    if (nsteps <= 0) return;
+    eam_forces_cta<real>(s, n, box, fs, nullptr);
+    bool bad = false;
+    if (L.scheme == PMD_SCHEME_PAPER) {
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k)
+#pragma unroll
+            for (int al = 0; al < 3; ++al) own.vh[k][al] = own.v[k][al];
+        for (int ell = 0; ell < nsteps; ++ell) {
+            const double s0 = sched_sigma(L, ell), s1 = sched_sigma(L, ell + 1);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int i = threadIdx.x + k * blockDim.x;
+                if (i >= n) break;
+                double G[3];
+                normals3(L.seed, nid, ell, i, G);
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    const double vhn = half_kick(L, own.v[k][al], s.F[al * n + i], own.vh[k][al], s0, G[al]);
+                    own.vh[k][al] = vhn;
+                    const double q0 = s.q[al * n + i];
+                    const double qn = drift(q0, L.dt, vhn);
+                    if (!isfinite(qn)) bad = true;
+                    if (fabs(qn - q0) > 0.5 * box[al]) flag(status, ST_LOSTATOM);
+                    s.q[al * n + i] = qn;
+                }
+                s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
+            }
+            __syncthreads();
+            eam_forces_cta<real>(s, n, box, fs, nullptr);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int i = threadIdx.x + k * blockDim.x;
+                if (i >= n) break;
+                double G[3];
+                normals3(L.seed, nid, ell + 1, i, G);
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+                    own.v[k][al] = half_kick(L, own.vh[k][al], s.F[al * n + i], own.vh[k][al], s1, G[al]);
+            }
+        }
+    } else {
+        for (int ell = 0; ell < nsteps; ++ell) {
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int i = threadIdx.x + k * blockDim.x;
+                if (i >= n) break;
+                double G[3];
+                normals3(L.seed, nid, ell, i, G);
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    double v = kick_b(L, own.v[k][al], s.F[al * n + i]);
+                    const double q0 = s.q[al * n + i];
+                    double q = __dadd_rn(q0, __dmul_rn(L.hdt, v));
+                    v = ou_o(L, v, G[al]);
+                    q = __dadd_rn(q, __dmul_rn(L.hdt, v));
+                    if (!isfinite(q)) bad = true;
+                    if (fabs(q - q0) > 0.5 * box[al]) flag(status, ST_LOSTATOM);
+                    s.q[al * n + i] = q;
+                    own.v[k][al] = v;
+                }
+                s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
+            }
+            __syncthreads();
+            eam_forces_cta<real>(s, n, box, fs, nullptr);
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {
+                const int i = threadIdx.x + k * blockDim.x;
+                if (i >= n) break;
+#pragma unroll
+                for (int al = 0; al < 3; ++al) own.v[k][al] = kick_b(L, own.v[k][al], s.F[al * n + i]);
+            }
+        }
+    }
+    if (bad) flag(status, ST_NONFINITE);
+}
+
+template <int KMAX>
+__device__ void load_state(const EamShared& s, OwnState<KMAX>& own, int n, const double* q, const double* v,
+                           const double box[3]) {
+    for (int x = threadIdx.x; x < 3 * n; x += blockDim.x) s.q[x] = q[x];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+#pragma unroll
+        for (int al = 0; al < 3; ++al) own.v[k][al] = i < n ? v[al * n + i] : 0.0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
+    __syncthreads();
+}
+
+template <int KMAX>
+__device__ void store_state(const EamShared& s, const OwnState<KMAX>& own, int n, double* q, double* v) {
+    __syncthreads();
+    for (int x = threadIdx.x; x < 3 * n; x += blockDim.x) q[x] = s.q[x];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        if (i < n) {
+#pragma unroll
+            for (int al = 0; al < 3; ++al) v[al * n + i] = own.v[k][al];
+        }
+    }
+}
+
+template <typename real, int KMAX>
+__global__ void __launch_bounds__(COARSE_MAX_THREADS) k_coarse_batch(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, double* q, double* v,
+                               long stride, const int32_t* __restrict__ nsteps, const int64_t* __restrict__ ids,
+                               int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const EamShared s = coarse_carve(smem, n);
+    const double box[3] = {b0, b1, b2};
+    const int m = blockIdx.x;
+    int Lm = nsteps[m];
+    if (Lm < 0 || (L.schedule == PMD_SCHED_L1_SYM && Lm > 1)) {
+        if (threadIdx.x == 0) flag(status, ST_BADARG);
+        return;
+    }
+    OwnState<KMAX> own;
+    load_state<KMAX>(s, own, n, q + m * stride, v + m * stride, box);
+    coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, Lm, ids[m], status);
+    store_state<KMAX>(s, own, n, q + m * stride, v + m * stride);
+}
+
+static void coarse_shape(int n, int& threads, int& kmax) {
+    threads = std::min(COARSE_MAX_THREADS, (n + 31) / 32 * 32);
+    kmax = (n + threads - 1) / threads;
+}
+
+int coarse_propagate(pmd_engine* e, int nbatch, int n, double* q, double* v, long stride, const int32_t* nsteps,
+                     const int64_t* ids, const pmd_langevin& lp, cudaStream_t st) {
+    int threads, kmax;
+    coarse_shape(n, threads, kmax);
+    const size_t sm = coarse_smem_bytes(n);
+    const FSDev fs = make_fs(e->p.coarse);
+    const LangevinDev L = make_langevin(lp);
+    const bool f64 = e->p.coarse.precision == PMD_FP64;
+    const double* B = e->p.box;
+    auto go = [&](auto kern) -> int {
+        PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        kern<<<nbatch, threads, sm, st>>>(n, B[0], B[1], B[2], fs, L, q, v, stride, nsteps, ids, e->status.as<int>());
+        PMD_CUDA_TRY(cudaGetLastError());
+        return PMD_OK;
+    };
+    if (kmax == 1) return f64 ? go(k_coarse_batch<double, 1>) : go(k_coarse_batch<float, 1>);
+    if (kmax == 2) return f64 ? go(k_coarse_batch<double, 2>) : go(k_coarse_batch<float, 2>);
+    if (kmax <= 4) return f64 ? go(k_coarse_batch<double, 4>) : go(k_coarse_batch<float, 4>);
+    return fail(PMD_EUNSUPPORTED, "coarse propagation supports at most 2048 atoms");
+}
+
+// ---- parareal correction sweep ---------------------------------------------------------------
+struct SweepResult {
+    double delta;
+    int n_stop;
+    int pad;
+};
+
+// deterministic CTA-wide sum (fixed tree) of one double per thread
+__device__ double cta_sum(double x, double* red) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = x;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+__device__ double cta_max(double x, double* red) {
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (l == 0) red[w] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double t = threadIdx.x < nw ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t = fmax(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <typename real, int KMAX>
+__global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, int nsteps, int n_in,
+                                 int n_fin, const double* __restrict__ jumps, const double* __restrict__ prev,
+                                 double* __restrict__ cur, double* __restrict__ cout, double delta_expl, int metric,
+                                 SweepResult* res, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const EamShared s = coarse_carve(smem, n);
+    __shared__ double red[33];
+    const double box[3] = {b0, b1, b2};
+    const long S = 6L * n;
+    OwnState<KMAX> own;
+    load_state<KMAX>(s, own, n, cur, cur + 3 * n, box);
+    // error sums start at n = n_in: |q^cur_{n_in} - q^prev_{n_in}| and |q^prev_{n_in}|
+    double num = 0.0, den = 0.0;
+    {
+        double a = 0.0, b = 0.0, mx = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double d2 = 0.0;
+            for (int al = 0; al < 3; ++al) {
+                const double c = cur[al * n + i], p = prev[al * n + i];
+                d2 += (c - p) * (c - p);
+                b += p * p;
+            }
+            a += d2;
+            mx = fmax(mx, sqrt(d2));
+        }
+        if (metric == PMD_METRIC_REL) {
+            num = sqrt(cta_sum(a, red));
+            den = sqrt(cta_sum(b, red));
+        } else {
+            num = cta_max(mx, red);
+        }
+    }
+    double delta = metric == PMD_METRIC_REL ? (den > 0 ? num / den : 0.0) : num;
+    int n_stop = n_fin;
+    for (int nn = n_in; nn < n_fin; ++nn) {
+        const long idx = nn - n_in;
+        coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, nsteps, (int64_t)nn, status);
+        __syncthreads();
+        double* co = cout + idx * S;
+        double* cn = cur + (idx + 1) * S;
+        const double* J = jumps ? jumps + idx * S : nullptr;
+        const double* P = prev + (idx + 1) * S;
+        double a = 0.0, b = 0.0, mx = 0.0;
+        bool bad = false;
+        for (int x = threadIdx.x; x < 3 * n; x += blockDim.x) {
+            const double c = s.q[x];
+            co[x] = c;
+            const double u = J ? c + J[x] : c;
+            s.q[x] = u;
+            cn[x] = u;
+            if (!isfinite(u)) bad = true;
+        }
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
+            if (i < n) {
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    const double c = own.v[k][al];
+                    co[3 * n + al * n + i] = c;
+                    const double u = J ? c + J[3 * n + al * n + i] : c;
+                    own.v[k][al] = u;
+                    cn[3 * n + al * n + i] = u;
+                    if (!isfinite(u)) bad = true;
+                }
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
+            double d2 = 0.0;
+            for (int al = 0; al < 3; ++al) {
+                const double c = s.q[al * n + i], p = P[al * n + i];
+                d2 += (c - p) * (c - p);
+                b += p * p;
+            }
+            a += d2;
+            mx = fmax(mx, sqrt(d2));
+        }
+        const int anybad = __syncthreads_or(bad ? 1 : 0);
+        if (metric == PMD_METRIC_REL) {
+            num += sqrt(cta_sum(a, red));
+            den += sqrt(cta_sum(b, red));
+            delta = num / den;
+        } else {
+            num = fmax(num, cta_max(mx, red));
+            delta = num;
+        }
+        if (anybad || !isfinite(delta)) delta = INFINITY;
+        if (!(delta <= delta_expl)) {
+            n_stop = nn;
+            break;
+        }
+    }
+    if (threadIdx.x == 0) {
+        res->delta = delta;
+        res->n_stop = n_stop;
+    }
+}
+
+int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, const double* prev, double* cur,
+                   double* cout, double delta_expl, int metric, int L, const pmd_langevin& lp, double* delta_host,
+                   int* n_stop_host, cudaStream_t st) {
+    const int n = e->p.natoms;
+    int threads, kmax;
+    coarse_shape(n, threads, kmax);
+    threads = std::max(threads, 64);
+    kmax = (n + threads - 1) / threads;
+    const size_t sm = coarse_smem_bytes(n);
+    const FSDev fs = make_fs(e->p.coarse);
+    const LangevinDev Ld = make_langevin(lp);
+    const bool f64 = e->p.coarse.precision == PMD_FP64;
+    const double* B = e->p.box;
+    SweepResult* res = e->s_result.as<SweepResult>();
+    auto go = [&](auto kern) -> int {
+        PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        kern<<<1, threads, sm, st>>>(n, B[0], B[1], B[2], fs, Ld, L, n_in, n_fin, jumps, prev, cur, cout, delta_expl,
+                                     metric, res, e->status.as<int>());
+        PMD_CUDA_TRY(cudaGetLastError());
+        return PMD_OK;
+    };
+    int rc;
+    if (kmax == 1) rc = f64 ? go(k_parareal_sweep<double, 1>) : go(k_parareal_sweep<float, 1>);
+    else if (kmax == 2) rc = f64 ? go(k_parareal_sweep<double, 2>) : go(k_parareal_sweep<float, 2>);
+    else if (kmax <= 4) rc = f64 ? go(k_parareal_sweep<double, 4>) : go(k_parareal_sweep<float, 4>);
+    else return fail(PMD_EUNSUPPORTED, "parareal_correct supports at most 2048 atoms");
+    if (rc) return rc;
+    SweepResult* h = static_cast<SweepResult*>(e->pinned);
+    PMD_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(SweepResult), cudaMemcpyDeviceToHost, st));
+    PMD_CUDA_TRY(cudaStreamSynchronize(st));
+    *delta_host = h->delta;
+    *n_stop_host = h->n_stop;
+    return PMD_OK;
+}
+
+// ---- jumps ------------------------------------------------------------------------------------
+__global__ void k_jumps(const double* __restrict__ f, const double* __restrict__ c, double* __restrict__ j, long count) {
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < count; x += (long)gridDim.x * blockDim.x)
+        j[x] = f[x] - c[x];
+}
+
+int jumps_launch(long count, const double* f, const double* c, double* j, int num_sms, cudaStream_t st) {
+    if (count <= 0) return PMD_OK;
+    const long blocks = std::min<long>((count + 255) / 256, (long)num_sms * 8);
+    k_jumps<<<(unsigned)blocks, 256, 0, st>>>(f, c, j, count);
+    PMD_CUDA_TRY(cudaGetLastError());
+    return PMD_OK;
+}
+
+}  // namespace pmd

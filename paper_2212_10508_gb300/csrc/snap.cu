@@ -1,0 +1,454 @@
+// SNAP: host-side tables (Clebsch-Gordan blocks, contraction schedule) and the kernels behind
+// snap_energy_forces (Sec. 3.1, fine potential).
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <numeric>
+#include <tuple>
+
+#include "pmd_internal.h"
+#include "snap_device.cuh"
+#include "snap_kernels.cuh"
+
+namespace pmd {
+
+// ---- Clebsch-Gordan <j1 m1 j2 m2 | J M> (doubled arguments), Racah's closed form ---------
+static double lfact(int n) { return std::lgamma((double)n + 1.0); }
+
+static double clebsch(int tj1, int tm1, int tj2, int tm2, int tJ, int tM) {
+    if (tm1 + tm2 != tM || std::abs(tm1) > tj1 || std::abs(tm2) > tj2 || std::abs(tM) > tJ) return 0.0;
+    if (tJ < std::abs(tj1 - tj2) || tJ > tj1 + tj2 || ((tj1 + tj2 + tJ) & 1)) return 0.0;
+    const int a = (tj1 + tj2 - tJ) / 2, b = (tj1 - tm1) / 2, c = (tj2 + tm2) / 2;
+    const int d = (tJ - tj2 + tm1) / 2, e = (tJ - tj1 - tm2) / 2;
+    const double lpre = 0.5 * (std::log((double)tJ + 1.0) + lfact((tJ + tj1 - tj2) / 2) + lfact((tJ - tj1 + tj2) / 2) +
+                               lfact(a) - lfact((tj1 + tj2 + tJ) / 2 + 1) + lfact((tj1 + tm1) / 2) + lfact(b) +
+                               lfact((tj2 - tm2) / 2) + lfact(c) + lfact((tJ + tM) / 2) + lfact((tJ - tM) / 2));
+    double s = 0.0;
+    const int zlo = std::max(0, std::max(-d, -e)), zhi = std::min(a, std::min(b, c));
+    for (int z = zlo; z <= zhi; ++z) {
+        double t = std::exp(lpre - lfact(z) - lfact(a - z) - lfact(b - z) - lfact(c - z) - lfact(d + z) - lfact(e + z));
+        s += (z & 1) ? -t : t;
+    }
+    return s;
+}
+
+int build_snap_tables(int twojmax, SnapHostTables* T) {
+    T->twojmax = twojmax;
+    T->tri.clear();
+    for (int tj1 = 0; tj1 <= twojmax; ++tj1)
+        for (int tj2 = 0; tj2 <= tj1; ++tj2)
+            for (int tj = tj1; tj <= twojmax; ++tj)
+                if (tj <= tj1 + tj2 && ((tj1 + tj2 + tj) & 1) == 0) {
+                    T->tri.push_back(tj1);
+                    T->tri.push_back(tj2);
+                    T->tri.push_back(tj);
+                }
+    T->nB = (int)T->tri.size() / 3;
+    T->hoff.assign(twojmax + 2, 0);
+    for (int tj = 0; tj <= twojmax; ++tj) T->hoff[tj + 1] = T->hoff[tj] + (tj + 1) * ncol_half(tj);
+    T->nhalf = T->hoff[twojmax + 1];
+    T->nfull = uoff_full(twojmax + 1);
+
+    // contraction blocks: dB_t = Re<Z^j_{j1j2}, dU^j> + (2j+1)/(2j1+1) Re<Z^{j1}_{j j2}, dU^{j1}>
+    //                            + (2j+1)/(2j2+1) Re<Z^{j2}_{j j1}, dU^{j2}>
+    std::map<std::tuple<int, int, int>, int> bid;   // (tj, ta, tb) -> block
+    std::vector<std::vector<std::pair<int, double>>> contrib;
+    auto add = [&](int tJ, int x, int y, int t, double coef) {
+        const int ta = std::max(x, y), tb = std::min(x, y);
+        auto key = std::make_tuple(tJ, ta, tb);
+        auto it = bid.find(key);
+        int id;
+        if (it == bid.end()) {
+            id = (int)contrib.size();
+            bid[key] = id;
+            contrib.emplace_back();
+        } else {
+            id = it->second;
+        }
+        contrib[id].push_back({t, coef});
+        return id;
+    };
+    T->tri_blk.assign(T->nB, -1);
+    for (int t = 0; t < T->nB; ++t) {
+        const int tj1 = T->tri[3 * t], tj2 = T->tri[3 * t + 1], tj = T->tri[3 * t + 2];
+        T->tri_blk[t] = add(tj, tj1, tj2, t, 1.0);
+        add(tj1, tj, tj2, t, (tj + 1.0) / (tj1 + 1.0));
+        add(tj2, tj, tj1, t, (tj + 1.0) / (tj2 + 1.0));
+    }
+    const int nblk = (int)contrib.size();
+    T->blk_ta.assign(nblk, 0);
+    T->blk_tb.assign(nblk, 0);
+    T->blk_tj.assign(nblk, 0);
+    T->blk_cgoff.assign(nblk, 0);
+    T->cg.clear();
+    for (auto& kv : bid) {
+        const int id = kv.second;
+        const int tJ = std::get<0>(kv.first), ta = std::get<1>(kv.first), tb = std::get<2>(kv.first);
+        T->blk_tj[id] = tJ;
+        T->blk_ta[id] = ta;
+        T->blk_tb[id] = tb;
+    }
+    for (int id = 0; id < nblk; ++id) {
+        const int ta = T->blk_ta[id], tb = T->blk_tb[id], tJ = T->blk_tj[id];
+        T->blk_cgoff[id] = (int)T->cg.size();
+        for (int p1 = 0; p1 <= ta; ++p1)
+            for (int p2 = 0; p2 <= tb; ++p2) {
+                const int tm1 = 2 * p1 - ta, tm2 = 2 * p2 - tb;
+                T->cg.push_back(clebsch(ta, tm1, tb, tm2, tJ, tm1 + tm2));
+            }
+    }
+    T->beff_ptr.assign(nblk + 1, 0);
+    T->beff_t.clear();
+    T->beff_c.clear();
+    for (int id = 0; id < nblk; ++id) {
+        for (auto& tc : contrib[id]) {
+            T->beff_t.push_back(tc.first);
+            T->beff_c.push_back(tc.second);
+        }
+        T->beff_ptr[id + 1] = (int)T->beff_t.size();
+    }
+
+    // Y jobs: every half element (tj, p, q) receives one job per block with J = tj
+    struct Job {
+        int e, blk, tj, p, q, s, ta, tb, cost;
+    };
+    std::vector<std::vector<Job>> per_e(T->nhalf);
+    std::vector<double> ecost(T->nhalf, 0.0);
+    T->total_terms = 0;
+    for (int tj = 0; tj <= twojmax; ++tj)
+        for (int p = 0; p <= tj; ++p)
+            for (int q = qlo(tj); q <= tj; ++q) {
+                const int e = T->hoff[tj] + p * ncol_half(tj) + (q - qlo(tj));
+                for (int id = 0; id < nblk; ++id) {
+                    if (T->blk_tj[id] != tj) continue;
+                    const int ta = T->blk_ta[id], tb = T->blk_tb[id];
+                    const int s = (ta + tb - tj) / 2;
+                    const int np1 = std::min(ta, p + s) - std::max(0, p + s - tb) + 1;
+                    const int nq1 = std::min(ta, q + s) - std::max(0, q + s - tb) + 1;
+                    if (np1 <= 0 || nq1 <= 0) continue;
+                    per_e[e].push_back({e, id, tj, p, q, s, ta, tb, np1 * nq1});
+                    ecost[e] += np1 * nq1 + 4;   // + per-job overhead
+                    T->total_terms += np1 * nq1;
+                }
+            }
+    // longest-processing-time assignment of whole elements to the 32 lanes of a warp
+    std::vector<int> order(T->nhalf);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ecost[x] > ecost[y]; });
+    std::vector<double> load(32, 0.0);
+    std::vector<std::vector<int>> lane_elems(32);
+    for (int e : order) {
+        int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        load[best] += ecost[e];
+        lane_elems[best].push_back(e);
+    }
+    T->jobs.clear();
+    for (int l = 0; l < 32; ++l) {
+        T->lane_begin[l] = (int)T->jobs.size() / 4;
+        std::sort(lane_elems[l].begin(), lane_elems[l].end());
+        for (int e : lane_elems[l])
+            for (const Job& j : per_e[e]) {
+                T->jobs.push_back(j.e | (j.blk << 16));
+                T->jobs.push_back(j.tj | (j.p << 5) | (j.q << 10) | (j.s << 15) | (j.ta << 20) | (j.tb << 25));
+                T->jobs.push_back(uoff_full(j.ta) | (uoff_full(j.tb) << 16));
+                T->jobs.push_back(T->blk_cgoff[j.blk]);
+            }
+    }
+    T->lane_begin[32] = (int)T->jobs.size() / 4;
+    return PMD_OK;
+}
+
+template <typename real>
+static void make_elems(const SnapHostTables& T, std::vector<UElem<real>>& out) {
+    out.assign(T.nhalf, UElem<real>{});
+    for (int tj = 0; tj <= T.twojmax; ++tj)
+        for (int p = 0; p <= tj; ++p)
+            for (int q = qlo(tj); q <= tj; ++q) {
+                const int e = T.hoff[tj] + p * ncol_half(tj) + (q - qlo(tj));
+                UElem<real> el{};
+                auto hidx = [&](int t, int pp, int qq) { return T.hoff[t] + pp * ncol_half(t) + (qq - qlo(t)); };
+                if (tj == 0) {
+                    el.src1 = el.src2 = 0;
+                    el.c1 = el.c2 = 0;
+                } else if (2 * q > tj) {            // m > 0
+                    el.src1 = p >= 1 ? hidx(tj - 1, p - 1, q - 1) : 0;
+                    el.src2 = p <= tj - 1 ? hidx(tj - 1, p, q - 1) : 0;
+                    el.c1 = (real)std::sqrt((double)p / q);
+                    el.c2 = (real)std::sqrt((double)(tj - p) / q);
+                } else {                            // m = 0
+                    el.src1 = p >= 1 ? hidx(tj - 1, p - 1, q) : 0;
+                    el.src2 = p <= tj - 1 ? hidx(tj - 1, p, q) : 0;
+                    el.c1 = (real)std::sqrt((double)p / (tj - q));
+                    el.c2 = (real)std::sqrt((double)(tj - p) / (tj - q));
+                    el.flags |= 1;
+                }
+                el.ufull = uoff_full(tj) + p * (tj + 1) + q;
+                if (2 * q > tj) {
+                    el.umir = uoff_full(tj) + (tj - p) * (tj + 1) + (tj - q);
+                    if ((p - q) & 1) el.flags |= 2;
+                } else {
+                    el.umir = -1;
+                }
+                el.y0 = el.ufull;
+                el.yp = q + 1 <= tj ? el.ufull + 1 : el.ufull;
+                el.ym = q - 1 >= 0 ? el.ufull - 1 : el.ufull;
+                const double wq = (2 * q > tj) ? 2.0 : 1.0;
+                el.cD = (real)(wq * (q - 0.5 * tj));
+                el.cP = (real)(wq * std::sqrt((double)(q + 1) * (tj - q)));
+                el.cQ = (real)(wq * std::sqrt((double)(tj - q + 1) * q));
+                el.cS = (real)wq;
+                out[e] = el;
+            }
+}
+
+template <typename real>
+static int upload_tables(pmd_snap* s) {
+    const SnapHostTables& T = s->T;
+    std::vector<UElem<real>> el;
+    make_elems<real>(T, el);
+    s->elem_bytes = sizeof(UElem<real>);
+    int rc;
+    if ((rc = s->d_elem.ensure(el.size() * sizeof(UElem<real>)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_elem.p, el.data(), el.size() * sizeof(UElem<real>), cudaMemcpyHostToDevice));
+    std::vector<real> cg(T.cg.begin(), T.cg.end());
+    if ((rc = s->d_cg.ensure(std::max<size_t>(1, cg.size()) * sizeof(real)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_cg.p, cg.data(), cg.size() * sizeof(real), cudaMemcpyHostToDevice));
+    const int nblk = (int)T.blk_ta.size();
+    std::vector<int4> blk(nblk);
+    for (int i = 0; i < nblk; ++i) blk[i] = make_int4(T.blk_ta[i], T.blk_tb[i], T.blk_tj[i], T.blk_cgoff[i]);
+    if ((rc = s->d_blk.ensure(nblk * sizeof(int4)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_blk.p, blk.data(), nblk * sizeof(int4), cudaMemcpyHostToDevice));
+    if ((rc = s->d_beffptr.ensure((nblk + 1) * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_beffptr.p, T.beff_ptr.data(), (nblk + 1) * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_befft.ensure(T.beff_t.size() * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_befft.p, T.beff_t.data(), T.beff_t.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_beffc.ensure(T.beff_c.size() * sizeof(double)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_beffc.p, T.beff_c.data(), T.beff_c.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if ((rc = s->d_jobs.ensure(std::max<size_t>(1, T.jobs.size()) * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_jobs.p, T.jobs.data(), T.jobs.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_lanebeg.ensure(33 * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_lanebeg.p, T.lane_begin, 33 * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<int4> tb(T.nB);
+    for (int t = 0; t < T.nB; ++t) {
+        const int b = T.tri_blk[t];
+        tb[t] = make_int4(b, T.blk_ta[b], T.blk_tb[b], T.blk_tj[b]);
+    }
+    if ((rc = s->d_triblk.ensure(std::max(1, T.nB) * sizeof(int4)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_triblk.p, tb.data(), T.nB * sizeof(int4), cudaMemcpyHostToDevice));
+    return PMD_OK;
+}
+
+int snap_upload(pmd_snap* s) {
+    return s->p.precision == PMD_FP64 ? upload_tables<double>(s) : upload_tables<float>(s);
+}
+
+SnapView snap_view(const pmd_snap* s, const double* beta) {
+    SnapView v;
+    v.elem = s->d_elem.p;
+    v.cg = s->d_cg.p;
+    v.beffptr = s->d_beffptr.as<int>();
+    v.befft = s->d_befft.as<int>();
+    v.beffc = s->d_beffc.as<double>();
+    v.jobs = s->d_jobs.as<int4>();
+    v.lane_begin = s->d_lanebeg.as<int>();
+    v.beta = beta;
+    v.nhalf = s->T.nhalf;
+    v.ncg = (int)s->T.cg.size();
+    v.nblk = (int)s->T.blk_ta.size();
+    v.nB = s->T.nB;
+    v.sp.rcut = s->p.rcut;
+    v.sp.rcut_f = (float)s->p.rcut;
+    v.sp.rfac0 = s->p.rfac0;
+    v.sp.switchflag = s->p.switchflag;
+    return v;
+}
+
+// ---- kernels of the standalone energy/force call ----------------------------------------
+
+__global__ void k_wrap_f32(const double* __restrict__ pos, int nbatch, int n, double b0, double b1, double b2,
+                           float4* __restrict__ qf) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nbatch * n) return;
+    const long bb = idx / n, i = idx % n;
+    const double* P = pos + bb * 3 * n;
+    double x = P[i], y = P[n + i], z = P[2 * n + i];
+    x -= b0 * floor(x / b0);
+    y -= b1 * floor(y / b1);
+    z -= b2 * floor(z / b2);
+    qf[idx] = make_float4((float)x, (float)y, (float)z, 0.f);
+}
+
+template <typename real, int TJ>
+__global__ void __launch_bounds__(SNAP_THREADS) k_snap_atoms(SnapView v, int nbatch, int n, double b0, double b1,
+                                                             double b2, const double* __restrict__ pos,
+                                                             const float4* __restrict__ qf, int* __restrict__ nbr,
+                                                             int* __restrict__ nnb, real* __restrict__ dedr,
+                                                             cplx<real>* __restrict__ utot, int* status) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, v);
+    snap_shared_load<real, TJ>(sh, v);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const double box[3] = {b0, b1, b2};
+    const long natoms_all = (long)nbatch * n;
+    const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+    for (long item = (long)blockIdx.x * (blockDim.x >> 5) + warp; item < natoms_all; item += nwarps) {
+        const long bb = item / n;
+        const int i = (int)(item % n);
+        snap_atom_warp<real, TJ>(sh.ws[warp], sh.elem, v.jobs, sh.lane_begin, sh.cg, sh.beff, v.sp, lane, n, i,
+                                 pos + bb * 3 * n, qf + bb * n, box, nbr + item * NMAX, nnb + item,
+                                 dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr, status);
+    }
+}
+
+// B_t of one atom from U_tot (full layout): Re sum_{m m'} conj(U^j) Z^j_{j1 j2}, FP64 accumulation.
+template <typename real, int TJ>
+__global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, long natoms_all, int nB,
+                                  const int4* __restrict__ triblk, const real* __restrict__ cg,
+                                  const int4* __restrict__ blk, double* __restrict__ Bout) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= natoms_all * nB) return;
+    const long ia = idx / nB;
+    const int t = (int)(idx % nB);
+    const int4 tb = triblk[t];
+    const int ta = tb.y, tbb = tb.z, tj = tb.w;
+    const int4 bk = blk[tb.x];
+    const real* c = cg + bk.w;
+    const cplx<real>* U = utot + ia * Dims<TJ>::NFULL;
+    const cplx<real>* Ua = U + f_off(ta);
+    const cplx<real>* Ub = U + f_off(tbb);
+    const cplx<real>* Uj = U + f_off(tj);
+    const int s = (ta + tbb - tj) / 2;
+    double B = 0.0;
+    for (int p = 0; p <= tj; ++p)
+        for (int q = 0; q <= tj; ++q) {
+            double zr = 0, zi = 0;
+            for (int p1 = max(0, p + s - tbb); p1 <= min(ta, p + s); ++p1) {
+                const int p2 = p + s - p1;
+                const double c1 = (double)c[p1 * (tbb + 1) + p2];
+                for (int q1 = max(0, q + s - tbb); q1 <= min(ta, q + s); ++q1) {
+                    const int q2 = q + s - q1;
+                    const double cc = c1 * (double)c[q1 * (tbb + 1) + q2];
+                    const cplx<real> x = Ua[p1 * (ta + 1) + q1], y = Ub[p2 * (tbb + 1) + q2];
+                    const double xr = x.re, xi = x.im, yr = y.re, yi = y.im;
+                    zr += cc * (xr * yr - xi * yi);
+                    zi += cc * (xr * yi + xi * yr);
+                }
+            }
+            const cplx<real> u = Uj[p * (tj + 1) + q];
+            B += (double)u.re * zr + (double)u.im * zi;
+        }
+    Bout[idx] = B;
+}
+
+template <typename real>
+__global__ void k_snap_gather(const int* __restrict__ nbr, const int* __restrict__ nnb,
+                              const real* __restrict__ dedr, int nbatch, int n, double* __restrict__ forces,
+                              int* status) {
+    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long)nbatch * n) return;
+    const long bb = idx / n;
+    const int k = (int)(idx % n);
+    double F[3];
+    gather_force<real>(nbr + bb * n * NMAX, nnb + bb * n, dedr + bb * n * NMAX * 3, k, F, status);
+    double* out = forces + bb * 3 * n;
+    out[k] = F[0];
+    out[n + k] = F[1];
+    out[2 * n + k] = F[2];
+}
+
+// per member: E = sum_i (beta_0 + sum_t beta_t B_it), sumB[t] = sum_i B_it; fixed order.
+__global__ void k_snap_energy(const double* __restrict__ B, int nbatch, int n, int nB, const double* __restrict__ beta,
+                              double* __restrict__ energy, double* __restrict__ sumB) {
+    const int bb = blockIdx.x;
+    const double* Bm = B + (long)bb * n * nB;
+    for (int t = threadIdx.x; t < nB; t += blockDim.x) {
+        if (sumB) {
+            double s = 0.0;
+            for (int i = 0; i < n; ++i) s += Bm[(long)i * nB + t];
+            sumB[(long)bb * (1 + nB) + 1 + t] = s;
+        }
+    }
+    if (threadIdx.x == 0) {
+        if (sumB) sumB[(long)bb * (1 + nB)] = (double)n;
+        if (energy) {
+            double E = 0.0;
+            for (int i = 0; i < n; ++i) {
+                double Ei = beta[0];
+                for (int t = 0; t < nB; ++t) Ei += beta[1 + t] * Bm[(long)i * nB + t];
+                E += Ei;
+            }
+            energy[bb] = E;
+        }
+    }
+}
+
+template <typename real, int TJ>
+static int launch_snap(pmd_snap* s, int nbatch, int n, const double box[3], const double* pos, const double* beta,
+                       double* energy, double* forces, double* sumB, cudaStream_t st) {
+    const long na = (long)nbatch * n;
+    SnapView v = snap_view(s, beta);
+    const bool want_B = energy || sumB;
+    float4* qf = s->s_qf.as<float4>();
+    if (sizeof(real) == 4) {
+        k_wrap_f32<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(pos, nbatch, n, box[0], box[1], box[2], qf);
+        PMD_CUDA_TRY(cudaGetLastError());
+    }
+    const size_t sm = snap_shared_bytes<real, TJ>(v);
+    static_assert(SNAP_THREADS % 32 == 0, "");
+    PMD_CUDA_TRY(cudaFuncSetAttribute(k_snap_atoms<real, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    long wpb = SNAP_THREADS / 32;
+    long blocks = (na + wpb - 1) / wpb;
+    k_snap_atoms<real, TJ><<<(unsigned)blocks, SNAP_THREADS, sm, st>>>(
+        v, nbatch, n, box[0], box[1], box[2], pos, qf, s->s_nbr.as<int>(), s->s_nnb.as<int>(), s->s_dedr.as<real>(),
+        want_B ? s->s_utot.as<cplx<real>>() : nullptr, s->s_status.as<int>());
+    PMD_CUDA_TRY(cudaGetLastError());
+    if (forces) {
+        k_snap_gather<real><<<(unsigned)((na + 127) / 128), 128, 0, st>>>(
+            s->s_nbr.as<int>(), s->s_nnb.as<int>(), s->s_dedr.as<real>(), nbatch, n, forces, s->s_status.as<int>());
+        PMD_CUDA_TRY(cudaGetLastError());
+    }
+    if (want_B) {
+        const long nt = na * s->T.nB;
+        k_snap_bispectrum<real, TJ><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(
+            s->s_utot.as<cplx<real>>(), na, s->T.nB, s->d_triblk.as<int4>(), s->d_cg.as<real>(), s->d_blk.as<int4>(),
+            s->s_B.as<double>());
+        PMD_CUDA_TRY(cudaGetLastError());
+        k_snap_energy<<<nbatch, 64, 0, st>>>(s->s_B.as<double>(), nbatch, n, s->T.nB, beta, energy, sumB);
+        PMD_CUDA_TRY(cudaGetLastError());
+    }
+    return PMD_OK;
+}
+
+int snap_reserve_impl(pmd_snap* s, long na) {
+    const size_t rs = s->p.precision == PMD_FP64 ? 8 : 4;
+    int rc;
+    if ((rc = s->s_nbr.ensure(na * NMAX * sizeof(int)))) return rc;
+    if ((rc = s->s_nnb.ensure(na * sizeof(int)))) return rc;
+    if ((rc = s->s_dedr.ensure(na * NMAX * 3 * rs))) return rc;
+    if ((rc = s->s_qf.ensure(na * sizeof(float4)))) return rc;
+    if ((rc = s->s_utot.ensure(na * (size_t)s->T.nfull * 2 * rs))) return rc;
+    if ((rc = s->s_B.ensure(na * (size_t)std::max(1, s->T.nB) * sizeof(double)))) return rc;
+    return PMD_OK;
+}
+
+int snap_compute(pmd_snap* s, int nbatch, int n, const double box[3], const double* pos, const double* beta,
+                 double* energy, double* forces, double* sumB, cudaStream_t st) {
+    int rc = snap_reserve_impl(s, (long)nbatch * n);
+    if (rc) return rc;
+    const bool f64 = s->p.precision == PMD_FP64;
+    switch (s->p.twojmax) {
+#define PMD_SNAP_CASE(TJV)                                                                                    \
+    case TJV:                                                                                                 \
+        return f64 ? launch_snap<double, TJV>(s, nbatch, n, box, pos, beta, energy, forces, sumB, st)         \
+                   : launch_snap<float, TJV>(s, nbatch, n, box, pos, beta, energy, forces, sumB, st);
+        PMD_SNAP_CASE(2)
+        PMD_SNAP_CASE(4)
+        PMD_SNAP_CASE(6)
+        PMD_SNAP_CASE(8)
+#undef PMD_SNAP_CASE
+    }
+    return fail(PMD_EUNSUPPORTED, "twojmax must be 2, 4, 6 or 8");
+}
+
+}  // namespace pmd

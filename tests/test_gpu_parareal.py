@@ -1,0 +1,104 @@
+"""GPU parareal against the oracle's Algorithm 2 transcription and the exactness property
+(Sec. 2.1: q^k_n = q^ref_n for n <= k).  Engine: SNAP 2J = 8 fine, Finnis-Sinclair coarse,
+the 55-atom W + SIA cell (3^3 cells), FP64."""
+import numpy as np
+import pytest
+
+import oracle as O
+from oracle import parareal as PR
+import paper_2212_10508_gb300 as P
+import workloads as W
+from gpu_util import N, T, dev, rel_max, torch
+
+pytestmark = pytest.mark.gpu
+
+DT, GAMMA, TEMP, SEED = 2e-3, 1.0, 2000.0, 31
+
+
+def _setup():
+    pos, box = W.bcc_sia(3)
+    q0 = W.displaced(pos, 0.05, W.rng(21, 1))
+    v0 = W.velocities(pos.shape[1], TEMP, W.rng(21, 2))
+    beta = W.snap_beta(55, W.rng(21, 3))
+    eng = P.Engine(pos.shape[1], box, P.snap_params(), P.fs_params(), beta=T(beta))
+    return q0, v0, box, beta, eng
+
+
+def _oracle_props(box, beta, L):
+    lp = O.langevin(dt=DT, gamma=GAMMA, T=TEMP, seed=SEED, schedule=O.SCHED_ROBUST)
+
+    def make(pot):
+        def prop(states, ns):
+            q = np.ascontiguousarray(np.array([s[0] for s in states]))
+            v = np.ascontiguousarray(np.array([s[1] for s in states]))
+            O.propagate(pot, q, v, box, [L] * len(ns), ns, lp)
+            return [(q[i], v[i]) for i in range(len(ns))]
+        return prop
+    return make(O.potential(O.POT_SNAP, beta=beta)), make(O.potential(O.POT_FS))
+
+
+@pytest.mark.parametrize("metric,dc,de", [(P.METRIC_REL, 1e-13, 1.0), (P.METRIC_MAXDISP, 1e-10, 4e-4)])
+def test_adaptive_parareal_matches_algorithm_2(metric, dc, de):
+    q0, v0, box, beta, eng = _setup()
+    Nint, L = 6, 2
+    lp = P.langevin(dt=DT, gamma=GAMMA, T=TEMP, seed=SEED, schedule=P.SCHED_ROBUST)
+    cur, st = P.adaptive_parareal(eng, T(q0), T(v0), Nint, L, dc, de, lp, metric=metric)
+    eng.sync_status()
+    F, C = _oracle_props(box, beta, L)
+    ocur, olog = PR.adaptive(q0, v0, Nint, dc, de, F, C, metric="rel" if metric == P.METRIC_REL else "maxdisp")
+    want = [(w["n_init"], e, k, i) for i, w in enumerate(olog.windows) for e, k in w["subs"]]
+    assert st.log() == want
+    g = N(cur)
+    for n in range(Nint + 1):
+        assert np.abs(g[n, :3] - ocur[n][0]).max() < 1e-8
+        assert np.abs(g[n, 3:] - ocur[n][1]).max() < 1e-6
+
+
+def test_exactness_k_ge_n_on_gpu():
+    """After k parareal iterations the first k intervals equal the sequential fine trajectory."""
+    q0, v0, box, beta, eng = _setup()
+    n_at = q0.shape[1]
+    Nint, L = 5, 3
+    lp = P.langevin(dt=DT, gamma=GAMMA, T=TEMP, seed=SEED)
+    ref = torch.empty(Nint + 1, 6, n_at, dtype=torch.float64, device=dev())
+    ref[0, :3], ref[0, 3:] = T(q0), T(v0)
+    for n in range(Nint):
+        s = ref[n:n + 1].clone()
+        eng.baoab_propagate_batch(P.FINE, s, None, T([L], torch.int32), T([n], torch.int64), lp)
+        ref[n + 1] = s[0]
+    cur = torch.zeros_like(ref)
+    cur[0] = ref[0]
+    cache = torch.zeros(Nint, 6, n_at, dtype=torch.float64, device=dev())
+    eng.parareal_correct(0, Nint, None, cur, cur, cache, float("inf"), P.METRIC_REL, L, lp)
+    ids = T(np.arange(Nint), torch.int64)
+    for k in range(1, Nint + 2):            # E = 0 once k >= N + 1 (Sec. 2.1)
+        prev = cur.clone()
+        fine = prev[:Nint].clone()
+        eng.baoab_propagate_batch(P.FINE, fine, None, T([L] * Nint, torch.int32), ids, lp)
+        jumps = torch.empty_like(fine)
+        eng.parareal_jumps(Nint, fine, cache, jumps)
+        delta, n_stop = eng.parareal_correct(0, Nint, jumps, prev, cur, cache, float("inf"), P.METRIC_REL, L, lp)
+        assert n_stop == Nint
+        kk = min(k, Nint)
+        d = (cur[:kk + 1] - ref[:kk + 1]).abs().max().item()
+        assert d < 1e-12
+    assert delta < 1e-14
+
+
+def test_correct_reports_explosion_and_nonfinite():
+    q0, v0, box, beta, eng = _setup()
+    n_at = q0.shape[1]
+    lp = P.langevin(dt=DT, gamma=GAMMA, T=TEMP, seed=SEED)
+    cur = torch.zeros(4, 6, n_at, dtype=torch.float64, device=dev())
+    cur[0, :3], cur[0, 3:] = T(q0), T(v0)
+    prev = cur.clone()
+    cache = torch.zeros(3, 6, n_at, dtype=torch.float64, device=dev())
+    jumps = torch.zeros(3, 6, n_at, dtype=torch.float64, device=dev())
+    jumps[1, 0, 0] = 0.5                    # a 0.5 Angstrom kick on atom 0 after interval 1
+    prev[1:] = cur[0]                       # prev far from the coarse path: large REL error
+    eng.parareal_correct(0, 3, None, prev, prev, torch.zeros_like(cache), float("inf"), P.METRIC_REL, 1, lp)
+    d, ns = eng.parareal_correct(0, 3, jumps, prev, cur, cache, 0.3, P.METRIC_MAXDISP, 1, lp)
+    assert ns == 1 and d > 0.3
+    jumps[0, 0, 3] = float("nan")
+    d, ns = eng.parareal_correct(0, 3, jumps, prev, cur, cache, 1e9, P.METRIC_REL, 1, lp)
+    assert ns == 0 and d == float("inf")
