@@ -124,6 +124,13 @@ int pmd_snap_num_coeffs(const pmd_snap* s);
  * calls that stay within this size). */
 int pmd_snap_reserve(pmd_snap* s, int nbatch, int natoms);
 
+/* Algorithmic FP operation counts of the SNAP force kernels, enumerated from the context's own
+ * tables (half-layout recursion, contraction jobs, force contraction): *per_pair = operations per
+ * neighbour pair (U recursion and accumulation, plus the dE/dr pass), *per_atom = operations per
+ * atom independent of its neighbour count (the Y contraction).  A complex multiply counts 6, a
+ * real fused multiply-add 2.  Used for roofline accounting; any pointer may be NULL. */
+int pmd_snap_flop_model(const pmd_snap* s, double* per_pair, double* per_atom);
+
 /* SNAP energies and forces of nbatch independent systems (Sec. 3.1).
  *   pos    [nbatch][3][natoms]  FP64 device, unwrapped Angstrom
  *   beta   [1+nB]               FP64 device, beta[0] = per-atom constant
@@ -163,6 +170,11 @@ int pmd_engine_set_beta(pmd_engine* e, const double* beta, pmd_stream_t stream);
 int pmd_engine_reserve(pmd_engine* e, int nbatch);
 /* Synchronises the stream and returns (and clears) the engine's device status. */
 int pmd_sync_status(pmd_engine* e, pmd_stream_t stream);
+
+/* Kernel timing hook for roofline accounting: while enabled, every FINE propagation records
+ * CUDA events around its persistent kernel on the call's stream.  *last_ms (may be NULL)
+ * receives the duration of the most recent such kernel (waits for it to finish), or -1 if none. */
+int pmd_engine_profile(pmd_engine* e, int enable, double* last_ms);
 
 /* Propagate nbatch independent systems, member b for nsteps[b] steps of the Langevin scheme
  * lp driven by the fine (PMD_FINE, SNAP) or coarse (PMD_COARSE, EAM) potential, with noise

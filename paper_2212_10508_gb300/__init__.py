@@ -64,9 +64,10 @@ class Action(ctypes.Structure):
                 ("open_slab", ctypes.c_int), ("k", ctypes.c_int)]
 
 
-EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_num_coeffs", "pmd_snap_reserve",
+EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_num_coeffs", "pmd_snap_flop_model",
+           "pmd_snap_reserve",
            "snap_energy_forces", "pmd_snap_sync_status", "eam_energy_forces", "pmd_engine_create",
-           "pmd_engine_destroy", "pmd_engine_set_beta", "pmd_engine_reserve", "pmd_sync_status",
+           "pmd_engine_destroy", "pmd_engine_set_beta", "pmd_engine_reserve", "pmd_engine_profile", "pmd_sync_status",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
            "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log"]
 
@@ -89,6 +90,7 @@ def lib():
     L.pmd_snap_destroy.argtypes = [vp]
     L.pmd_snap_num_coeffs.argtypes = [vp]
     L.pmd_snap_reserve.argtypes = [vp, i32, i32]
+    L.pmd_snap_flop_model.argtypes = [vp, dp, dp]
     L.snap_energy_forces.argtypes = [vp, i32, i32, dp, vp, vp, vp, vp, vp, vp]
     L.pmd_snap_sync_status.argtypes = [vp, vp]
     L.eam_energy_forces.argtypes = [ctypes.POINTER(FSParams), i32, i32, dp, vp, vp, vp, vp]
@@ -96,6 +98,7 @@ def lib():
     L.pmd_engine_destroy.argtypes = [vp]
     L.pmd_engine_set_beta.argtypes = [vp, vp, vp]
     L.pmd_engine_reserve.argtypes = [vp, i32]
+    L.pmd_engine_profile.argtypes = [vp, i32, dp]
     L.pmd_sync_status.argtypes = [vp, vp]
     L.baoab_propagate_batch.argtypes = [vp, i32, i32, i32, vp, vp, i64, vp, vp, ctypes.POINTER(Langevin), vp]
     L.parareal_jumps.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -168,6 +171,12 @@ class Snap:
     def reserve(self, nbatch, natoms):
         _check(lib().pmd_snap_reserve(self.h, nbatch, natoms))
 
+    def flop_model(self):
+        """(operations per neighbour pair, operations per atom) of the force kernels."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        _check(lib().pmd_snap_flop_model(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
     def sync_status(self, stream=None):
         _check(lib().pmd_snap_sync_status(self.h, _stream(stream)))
 
@@ -223,6 +232,12 @@ class Engine:
 
     def sync_status(self, stream=None):
         _check(lib().pmd_sync_status(self.h, _stream(stream)))
+
+    def profile(self, enable=True):
+        """Enable/disable kernel timing; returns the last persistent-kernel duration in ms (or -1)."""
+        ms = ctypes.c_double()
+        _check(lib().pmd_engine_profile(self.h, 1 if enable else 0, ctypes.byref(ms)))
+        return ms.value
 
     def baoab_propagate_batch(self, potential, q, v, nsteps, interval_id, lp: Langevin, stream=None):
         """Propagate members in place.  q, v: [nb,3,n]; or v=None and q packed states [nb,6,n]

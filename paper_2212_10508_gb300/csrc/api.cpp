@@ -160,6 +160,21 @@ int pmd_snap_num_coeffs(const pmd_snap* s) {
     return 1 + s->T.nB;
 }
 
+int pmd_snap_flop_model(const pmd_snap* s, double* per_pair, double* per_atom) {
+    if (!s) return fail(PMD_EINVAL, "pmd_snap_flop_model: NULL context");
+    const double nh = (double)s->T.nhalf;
+    // per neighbour: U pass (2 complex products, 2 scaled adds, weighted accumulation: 20 per
+    // element) + force pass (recursion 16 + 3 conj-products 18 + 7 real multiply-adds 14 per
+    // element) + the warp reduction and the final 3-component contraction (~120)
+    const double pair = nh * 20.0 + nh * 48.0 + 120.0;
+    // per atom: Y contraction, 10 per Clebsch-Gordan term (complex product 6, scaled add 4),
+    // plus 4 per (job, row) for the outer scaled add (bounded by the term count / 2)
+    const double atom = 10.0 * s->T.total_terms + 2.0 * s->T.total_terms;
+    if (per_pair) *per_pair = pair;
+    if (per_atom) *per_atom = atom;
+    return PMD_OK;
+}
+
 int pmd_snap_reserve(pmd_snap* s, int nbatch, int natoms) {
     if (!s || nbatch < 0 || natoms < 0) return fail(PMD_EINVAL, "pmd_snap_reserve: bad arguments");
     return snap_reserve_impl(s, (long)nbatch * natoms);
@@ -233,6 +248,8 @@ int pmd_engine_destroy(pmd_engine* e) {
                       &e->s_result};
     for (DevBuf* b : bufs) b->release();
     if (e->pinned) cudaFreeHost(e->pinned);
+    if (e->ev0) cudaEventDestroy(e->ev0);
+    if (e->ev1) cudaEventDestroy(e->ev1);
     pmd_snap_destroy(e->snap);
     delete e;
     return PMD_OK;
@@ -255,6 +272,25 @@ int pmd_engine_reserve(pmd_engine* e, int nbatch) {
         (rc = e->s_vh.ensure(na * 3 * sizeof(double))) || (rc = e->s_order.ensure((2 * (size_t)nbatch + 4) * sizeof(int))))
         return rc;
     e->cap_batch = nbatch;
+    return PMD_OK;
+}
+
+int pmd_engine_profile(pmd_engine* e, int enable, double* last_ms) {
+    if (!e) return fail(PMD_EINVAL, "pmd_engine_profile: NULL engine");
+    if (enable && !e->ev0) {
+        PMD_CUDA_TRY(cudaEventCreate(&e->ev0));
+        PMD_CUDA_TRY(cudaEventCreate(&e->ev1));
+    }
+    if (last_ms) {
+        *last_ms = -1.0;
+        if (e->prof_recorded) {
+            float ms = 0.f;
+            PMD_CUDA_TRY(cudaEventSynchronize(e->ev1));
+            PMD_CUDA_TRY(cudaEventElapsedTime(&ms, e->ev0, e->ev1));
+            *last_ms = ms;
+        }
+    }
+    e->profile = enable ? 1 : 0;
     return PMD_OK;
 }
 

@@ -95,6 +95,9 @@ struct pmd_engine {
     int device = 0;
     int num_sms = 0;
     void* pinned = nullptr;          // small pinned host buffer for parareal_correct results
+    int profile = 0;                 // record events around the persistent FINE kernel
+    int prof_recorded = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
 struct pmd_adaptive;  // defined in adaptive.cpp

@@ -11,11 +11,15 @@ Recipe (stated again in the design doc):
     s +- 1.1 Angstrom * (1,1,1)/sqrt(3)  (2 n^3 + 1 atoms);
   * displacements: i.i.d. N(0, sigma^2) per coordinate (sigma = 0.05 Angstrom);
   * velocities: i.i.d. N(0, k_B T / m) per coordinate, centre-of-mass velocity removed;
-  * SNAP coefficients: beta_0 = -8.9 eV, beta_t ~ N(0, 0.01^2);
+  * SNAP coefficients: beta_0 = -8.9 eV, beta_t ~ N(0, 0.01^2) (parity inputs), or the
+    coefficients fitted to Finnis-Sinclair tungsten stored in tests/golden/beta_fs_w_2j8.txt
+    (long trajectories: random coefficients have no repulsive core and the cell collapses);
   * interval lengths: L_b ~ U{100, ..., 2000}.
 Every draw comes from numpy's PCG64 seeded by a SplitMix64-derived sub-seed of one
 master seed, so each stream is reproducible on its own.
 """
+import os
+
 import numpy as np
 
 A_W = 3.1652             # BCC tungsten lattice constant, Angstrom
@@ -89,6 +93,15 @@ def snap_beta(nB, gen: np.random.Generator, std=0.01, beta0=BETA0):
     return b
 
 
+GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
+
+
+def fitted_beta():
+    """SNAP 2J=8 coefficients (1 + 55) fitted to Finnis-Sinclair W (see tests/golden/make_fitted_beta.py)."""
+    vals = [float(ln) for ln in open(os.path.join(GOLDEN, "beta_fs_w_2j8.txt")) if ln.strip() and ln[0] != "#"]
+    return np.array(vals)
+
+
 def n_bispectrum(twojmax: int) -> int:
     """Number of triples j2 <= j1 <= j <= J/2 with j <= j1 + j2 and integer j1+j2+j."""
     c = 0
@@ -114,13 +127,15 @@ def small_system(master=2212, nconf=16, sigma=0.05, twojmax=8):
     return P, box, beta
 
 
-def batch_workload(master=2212, nbatch=64, T=1500.0, lo=100, hi=2000, ncell=4, sigma=0.05, twojmax=8):
-    """nbatch members of the (ncell^3 + SIA) system with uneven lengths L_b ~ U{lo..hi}."""
+def batch_workload(master=2212, nbatch=64, T=1500.0, lo=100, hi=2000, ncell=4, sigma=0.05, twojmax=8,
+                   fitted=True):
+    """nbatch members of the (ncell^3 + SIA) system with uneven lengths L_b ~ U{lo..hi};
+    fitted=True uses the coefficients fitted to Finnis-Sinclair W, else random ones."""
     pos, box = bcc_sia(ncell)
     n = pos.shape[1]
     q = displaced(pos, sigma, rng(master, 11), count=nbatch)
     v = velocities(n, T, rng(master, 12), count=nbatch)
-    beta = snap_beta(n_bispectrum(twojmax), rng(master, 2))
+    beta = fitted_beta() if (fitted and twojmax == 8) else snap_beta(n_bispectrum(twojmax), rng(master, 2))
     L = interval_lengths(nbatch, rng(master, 13), lo, hi)
     ids = np.arange(nbatch, dtype=np.int64)
     return q, v, box, beta, L, ids
