@@ -147,8 +147,8 @@ int pmd_snap_create(const pmd_snap_params* p, pmd_snap** out) {
 
 int pmd_snap_destroy(pmd_snap* s) {
     if (!s) return PMD_OK;
-    DevBuf* bufs[] = {&s->d_elem, &s->d_cg, &s->d_blk, &s->d_beffptr, &s->d_befft, &s->d_beffc, &s->d_jobs,
-                      &s->d_lanebeg, &s->d_triblk, &s->s_nbr, &s->s_nnb, &s->s_dedr, &s->s_qf, &s->s_utot,
+    DevBuf* bufs[] = {&s->d_cg, &s->d_blk, &s->d_beffptr, &s->d_befft, &s->d_beffc, &s->d_jobs,
+                      &s->d_roundtb, &s->d_triblk, &s->s_nbr, &s->s_nnb, &s->s_dedr, &s->s_qf, &s->s_utot,
                       &s->s_B, &s->s_status};
     for (DevBuf* b : bufs) b->release();
     delete s;
@@ -163,13 +163,12 @@ int pmd_snap_num_coeffs(const pmd_snap* s) {
 int pmd_snap_flop_model(const pmd_snap* s, double* per_pair, double* per_atom) {
     if (!s) return fail(PMD_EINVAL, "pmd_snap_flop_model: NULL context");
     const double nh = (double)s->T.nhalf;
-    // per neighbour: U pass (2 complex products, 2 scaled adds, weighted accumulation: 20 per
-    // element) + force pass (recursion 16 + 3 conj-products 18 + 7 real multiply-adds 14 per
-    // element) + the warp reduction and the final 3-component contraction (~120)
-    const double pair = nh * 20.0 + nh * 48.0 + 120.0;
-    // per atom: Y contraction, 10 per Clebsch-Gordan term (complex product 6, scaled add 4),
-    // plus 4 per (job, row) for the outer scaled add (bounded by the term count / 2)
-    const double atom = 10.0 * s->T.total_terms + 2.0 * s->T.total_terms;
+    // per neighbour, per half element: U pass = recursion (two complex products 12, two scaled
+    // adds 4) + weighting 2 + the sum over neighbours 2; dE/dr pass = recursion 16 + contraction
+    // with the four weighted Y copies (2 + 2 + 4 + 4); plus ~100 for the final 3-component step
+    const double pair = nh * (16.0 + 2.0 + 2.0) + nh * (16.0 + 12.0) + 100.0;
+    // per atom: the Y contraction, 10 per Clebsch-Gordan term (complex product 6, scaled add 4)
+    const double atom = 10.0 * s->T.total_terms;
     if (per_pair) *per_pair = pair;
     if (per_atom) *per_atom = atom;
     return PMD_OK;

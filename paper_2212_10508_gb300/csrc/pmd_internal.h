@@ -55,10 +55,12 @@ struct SnapHostTables {
     std::vector<int> beff_ptr;        // CSR over blocks: contributions (t, coef)
     std::vector<int> beff_t;
     std::vector<double> beff_c;
-    // Y jobs: per lane a contiguous list, packed int4 {e | blk<<16, tj|p<<8|q<<16|s<<24, ta|tb<<8, cgoff}
-    std::vector<int> jobs;            // [njobs][4]
-    int lane_begin[33];
-    double total_terms = 0;           // CG terms per atom (for the flop model)
+    // Y jobs in lockstep rounds: [nrounds][32] int4 records, every round one sub-block size tb
+    std::vector<int> jobs;            // [nrounds * 32][4]
+    std::vector<unsigned char> round_tb;
+    int nrounds = 0;
+    double total_terms = 0;           // Clebsch-Gordan terms per atom (algorithmic, unpadded)
+    double padded_terms = 0;          // term slots executed (lockstep padding included)
     // bispectrum jobs (energy path): per triple t the block id of (j1, j2, j)
     std::vector<int> tri_blk;
 };
@@ -72,17 +74,15 @@ struct pmd_snap {
     pmd::SnapHostTables T;
     int device = 0;
     // device copies of the tables
-    pmd::DevBuf d_elem;      // packed per-half-element records (precision dependent)
     pmd::DevBuf d_cg;        // CG values (precision dependent)
     pmd::DevBuf d_blk;       // int4 per block {ta, tb, tj, cgoff}
     pmd::DevBuf d_beffptr, d_befft, d_beffc;
-    pmd::DevBuf d_jobs;      // int4 jobs
-    pmd::DevBuf d_lanebeg;   // int[33]
+    pmd::DevBuf d_jobs;      // int4 jobs [nrounds][32]
+    pmd::DevBuf d_roundtb;   // uint8 [nrounds]
     pmd::DevBuf d_triblk;    // int4 per triple {blk, ta, tb, tj}
     // scratch
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_utot, s_B, s_status;
     int cap_atoms = 0;
-    size_t elem_bytes = 0;   // bytes of one element record
 };
 
 struct pmd_engine {

@@ -205,9 +205,9 @@ __global__ void __launch_bounds__(FINE_THREADS) k_fine_persistent(FineArgs a) {
             const int m = a.order[it / n];
             const int i = (int)(it % n);
             real* dd = (real*)a.dedr + ((long)m * n + i) * NMAX * 3;
-            snap_atom_warp<real, TJ>(sh.ws[warp], sh.elem, a.v.jobs, sh.lane_begin, sh.cg, sh.beff, a.v.sp, lane, n,
-                                     i, a.q + m * a.stride, a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX,
-                                     a.nnb + (long)m * n + i, dd, nullptr, a.status);
+            snap_atom_warp2<real, TJ>(sh.ws[warp], a.v.yt, sh.cg, sh.beff, a.v.sp, lane, n, i, a.q + m * a.stride,
+                                      a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX,
+                                      a.nnb + (long)m * n + i, dd, nullptr, a.status);
         }
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
         for (long it = gtid; it < items; it += nthreads) {

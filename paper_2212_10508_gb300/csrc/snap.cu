@@ -7,7 +7,6 @@
 #include <tuple>
 
 #include "pmd_internal.h"
-#include "snap_device.cuh"
 #include "snap_kernels.cuh"
 
 namespace pmd {
@@ -108,12 +107,12 @@ int build_snap_tables(int twojmax, SnapHostTables* T) {
         T->beff_ptr[id + 1] = (int)T->beff_t.size();
     }
 
-    // Y jobs: every half element (tj, p, q) receives one job per block with J = tj
+    // Y jobs: every half element e = (tj, p, q) (row-major half index) receives one job per
+    // block (ta, tb, J = tj); a job is a (tb+1) x (tb+1) loop over p1 = p+s-tb+i, q1 = q+s-tb+k.
     struct Job {
-        int e, blk, tj, p, q, s, ta, tb, cost;
+        int e, blk, tb, p10, q10, ta;
     };
     std::vector<std::vector<Job>> per_e(T->nhalf);
-    std::vector<double> ecost(T->nhalf, 0.0);
     T->total_terms = 0;
     for (int tj = 0; tj <= twojmax; ++tj)
         for (int p = 0; p <= tj; ++p)
@@ -126,90 +125,85 @@ int build_snap_tables(int twojmax, SnapHostTables* T) {
                     const int np1 = std::min(ta, p + s) - std::max(0, p + s - tb) + 1;
                     const int nq1 = std::min(ta, q + s) - std::max(0, q + s - tb) + 1;
                     if (np1 <= 0 || nq1 <= 0) continue;
-                    per_e[e].push_back({e, id, tj, p, q, s, ta, tb, np1 * nq1});
-                    ecost[e] += np1 * nq1 + 4;   // + per-job overhead
+                    per_e[e].push_back({e, id, tb, p + s - tb, q + s - tb, ta});
                     T->total_terms += np1 * nq1;
                 }
             }
-    // longest-processing-time assignment of whole elements to the 32 lanes of a warp
+    // assign whole outputs to lanes so that, per sub-block size tb, the largest per-lane job
+    // count (the number of lockstep rounds of that size) stays small
+    const int NTB = twojmax + 1;
+    auto w2 = [](int tb) { return (double)(tb + 1) * (tb + 1); };
+    std::vector<std::vector<int>> cnt(32, std::vector<int>(NTB, 0));
+    std::vector<int> mx(NTB, 0);
+    std::vector<double> load(32, 0.0);
     std::vector<int> order(T->nhalf);
     std::iota(order.begin(), order.end(), 0);
+    std::vector<double> ecost(T->nhalf, 0.0);
+    for (int e = 0; e < T->nhalf; ++e)
+        for (const Job& j : per_e[e]) ecost[e] += w2(j.tb);
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return ecost[x] > ecost[y]; });
-    std::vector<double> load(32, 0.0);
-    std::vector<std::vector<int>> lane_elems(32);
+    std::vector<std::vector<int>> lane_out(32);
     for (int e : order) {
-        int best = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        std::vector<int> c(NTB, 0);
+        for (const Job& j : per_e[e]) c[j.tb] += 1;
+        int best = 0;
+        double best_inc = 1e300, best_load = 1e300;
+        for (int l = 0; l < 32; ++l) {
+            double inc = 0.0;
+            for (int tb = 0; tb < NTB; ++tb)
+                if (c[tb]) inc += w2(tb) * std::max(0, cnt[l][tb] + c[tb] - mx[tb]);
+            if (inc < best_inc || (inc == best_inc && load[l] < best_load)) {
+                best = l;
+                best_inc = inc;
+                best_load = load[l];
+            }
+        }
+        for (int tb = 0; tb < NTB; ++tb) {
+            cnt[best][tb] += c[tb];
+            mx[tb] = std::max(mx[tb], cnt[best][tb]);
+        }
         load[best] += ecost[e];
-        lane_elems[best].push_back(e);
+        lane_out[best].push_back(e);
     }
+    // rounds: for each tb, mx[tb] rounds; lane l runs its k-th job of that size in round k
     T->jobs.clear();
-    for (int l = 0; l < 32; ++l) {
-        T->lane_begin[l] = (int)T->jobs.size() / 4;
-        std::sort(lane_elems[l].begin(), lane_elems[l].end());
-        for (int e : lane_elems[l])
-            for (const Job& j : per_e[e]) {
-                T->jobs.push_back(j.e | (j.blk << 16));
-                T->jobs.push_back(j.tj | (j.p << 5) | (j.q << 10) | (j.s << 15) | (j.ta << 20) | (j.tb << 25));
-                T->jobs.push_back(uoff_full(j.ta) | (uoff_full(j.tb) << 16));
-                T->jobs.push_back(T->blk_cgoff[j.blk]);
+    T->round_tb.clear();
+    T->padded_terms = 0;
+    for (int tb = 0; tb < NTB; ++tb) {
+        std::vector<std::vector<Job>> lj(32);
+        for (int l = 0; l < 32; ++l) {
+            std::sort(lane_out[l].begin(), lane_out[l].end());
+            for (int e : lane_out[l])
+                for (const Job& j : per_e[e])
+                    if (j.tb == tb) lj[l].push_back(j);
+        }
+        for (int r = 0; r < mx[tb]; ++r) {
+            T->round_tb.push_back((unsigned char)tb);
+            T->padded_terms += 32.0 * w2(tb);
+            for (int l = 0; l < 32; ++l) {
+                if (r < (int)lj[l].size()) {
+                    const Job& j = lj[l][r];
+                    T->jobs.push_back(j.e | (j.blk << 16));
+                    T->jobs.push_back((j.p10 + 32) | ((j.q10 + 32) << 8) | (j.ta << 16) | (tb << 24));
+                    T->jobs.push_back(uoff_full(j.ta) | (uoff_full(tb) << 16));
+                    T->jobs.push_back(T->blk_cgoff[j.blk]);
+                } else {   // padding: every row/column out of range, output = the dummy slot
+                    T->jobs.push_back(T->nhalf);
+                    T->jobs.push_back(0 | (0 << 8) | (tb << 16) | (tb << 24));
+                    T->jobs.push_back(0);
+                    T->jobs.push_back(0);
+                }
             }
+        }
     }
-    T->lane_begin[32] = (int)T->jobs.size() / 4;
+    T->nrounds = (int)T->round_tb.size();
     return PMD_OK;
-}
-
-template <typename real>
-static void make_elems(const SnapHostTables& T, std::vector<UElem<real>>& out) {
-    out.assign(T.nhalf, UElem<real>{});
-    for (int tj = 0; tj <= T.twojmax; ++tj)
-        for (int p = 0; p <= tj; ++p)
-            for (int q = qlo(tj); q <= tj; ++q) {
-                const int e = T.hoff[tj] + p * ncol_half(tj) + (q - qlo(tj));
-                UElem<real> el{};
-                auto hidx = [&](int t, int pp, int qq) { return T.hoff[t] + pp * ncol_half(t) + (qq - qlo(t)); };
-                if (tj == 0) {
-                    el.src1 = el.src2 = 0;
-                    el.c1 = el.c2 = 0;
-                } else if (2 * q > tj) {            // m > 0
-                    el.src1 = p >= 1 ? hidx(tj - 1, p - 1, q - 1) : 0;
-                    el.src2 = p <= tj - 1 ? hidx(tj - 1, p, q - 1) : 0;
-                    el.c1 = (real)std::sqrt((double)p / q);
-                    el.c2 = (real)std::sqrt((double)(tj - p) / q);
-                } else {                            // m = 0
-                    el.src1 = p >= 1 ? hidx(tj - 1, p - 1, q) : 0;
-                    el.src2 = p <= tj - 1 ? hidx(tj - 1, p, q) : 0;
-                    el.c1 = (real)std::sqrt((double)p / (tj - q));
-                    el.c2 = (real)std::sqrt((double)(tj - p) / (tj - q));
-                    el.flags |= 1;
-                }
-                el.ufull = uoff_full(tj) + p * (tj + 1) + q;
-                if (2 * q > tj) {
-                    el.umir = uoff_full(tj) + (tj - p) * (tj + 1) + (tj - q);
-                    if ((p - q) & 1) el.flags |= 2;
-                } else {
-                    el.umir = -1;
-                }
-                el.y0 = el.ufull;
-                el.yp = q + 1 <= tj ? el.ufull + 1 : el.ufull;
-                el.ym = q - 1 >= 0 ? el.ufull - 1 : el.ufull;
-                const double wq = (2 * q > tj) ? 2.0 : 1.0;
-                el.cD = (real)(wq * (q - 0.5 * tj));
-                el.cP = (real)(wq * std::sqrt((double)(q + 1) * (tj - q)));
-                el.cQ = (real)(wq * std::sqrt((double)(tj - q + 1) * q));
-                el.cS = (real)wq;
-                out[e] = el;
-            }
 }
 
 template <typename real>
 static int upload_tables(pmd_snap* s) {
     const SnapHostTables& T = s->T;
-    std::vector<UElem<real>> el;
-    make_elems<real>(T, el);
-    s->elem_bytes = sizeof(UElem<real>);
     int rc;
-    if ((rc = s->d_elem.ensure(el.size() * sizeof(UElem<real>)))) return rc;
-    PMD_CUDA_TRY(cudaMemcpy(s->d_elem.p, el.data(), el.size() * sizeof(UElem<real>), cudaMemcpyHostToDevice));
     std::vector<real> cg(T.cg.begin(), T.cg.end());
     if ((rc = s->d_cg.ensure(std::max<size_t>(1, cg.size()) * sizeof(real)))) return rc;
     PMD_CUDA_TRY(cudaMemcpy(s->d_cg.p, cg.data(), cg.size() * sizeof(real), cudaMemcpyHostToDevice));
@@ -226,8 +220,8 @@ static int upload_tables(pmd_snap* s) {
     PMD_CUDA_TRY(cudaMemcpy(s->d_beffc.p, T.beff_c.data(), T.beff_c.size() * sizeof(double), cudaMemcpyHostToDevice));
     if ((rc = s->d_jobs.ensure(std::max<size_t>(1, T.jobs.size()) * sizeof(int)))) return rc;
     PMD_CUDA_TRY(cudaMemcpy(s->d_jobs.p, T.jobs.data(), T.jobs.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if ((rc = s->d_lanebeg.ensure(33 * sizeof(int)))) return rc;
-    PMD_CUDA_TRY(cudaMemcpy(s->d_lanebeg.p, T.lane_begin, 33 * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_roundtb.ensure(std::max<size_t>(1, T.round_tb.size())))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_roundtb.p, T.round_tb.data(), T.round_tb.size(), cudaMemcpyHostToDevice));
     std::vector<int4> tb(T.nB);
     for (int t = 0; t < T.nB; ++t) {
         const int b = T.tri_blk[t];
@@ -244,15 +238,14 @@ int snap_upload(pmd_snap* s) {
 
 SnapView snap_view(const pmd_snap* s, const double* beta) {
     SnapView v;
-    v.elem = s->d_elem.p;
     v.cg = s->d_cg.p;
     v.beffptr = s->d_beffptr.as<int>();
     v.befft = s->d_befft.as<int>();
     v.beffc = s->d_beffc.as<double>();
-    v.jobs = s->d_jobs.as<int4>();
-    v.lane_begin = s->d_lanebeg.as<int>();
+    v.yt.jobs = s->d_jobs.as<int4>();
+    v.yt.round_tb = s->d_roundtb.as<unsigned char>();
+    v.yt.nrounds = s->T.nrounds;
     v.beta = beta;
-    v.nhalf = s->T.nhalf;
     v.ncg = (int)s->T.cg.size();
     v.nblk = (int)s->T.blk_ta.size();
     v.nB = s->T.nB;
@@ -295,9 +288,9 @@ __global__ void __launch_bounds__(SNAP_THREADS) k_snap_atoms(SnapView v, int nba
     for (long item = (long)blockIdx.x * (blockDim.x >> 5) + warp; item < natoms_all; item += nwarps) {
         const long bb = item / n;
         const int i = (int)(item % n);
-        snap_atom_warp<real, TJ>(sh.ws[warp], sh.elem, v.jobs, sh.lane_begin, sh.cg, sh.beff, v.sp, lane, n, i,
-                                 pos + bb * 3 * n, qf + bb * n, box, nbr + item * NMAX, nnb + item,
-                                 dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr, status);
+        snap_atom_warp2<real, TJ>(sh.ws[warp], v.yt, sh.cg, sh.beff, v.sp, lane, n, i, pos + bb * 3 * n, qf + bb * n,
+                                  box, nbr + item * NMAX, nnb + item, dedr + item * NMAX * 3,
+                                  utot ? utot + item * Dims<TJ>::NFULL : nullptr, status);
     }
 }
 
