@@ -144,6 +144,22 @@ int snap_energy_forces(pmd_snap* s, int nbatch, int natoms, const double box[3],
 /* Synchronises the stream and returns (and clears) the context's device status. */
 int pmd_snap_sync_status(pmd_snap* s, pmd_stream_t stream);
 
+/* The same energies, forces and dE/dbeta as snap_energy_forces, for callers that may not
+ * allocate device memory while they run (an application that owns all device memory through
+ * its own allocator, a loop where cudaMalloc would stall or is not allowed, a fixed memory
+ * budget).  The paper has no counterpart; it is an interface addition of this library.
+ * Scratch comes from one array of PMD_NOALLOC_SCRATCH_BYTES compiled into the library and
+ * resident on every device that loads it; the call allocates nothing.  The context s must
+ * exist already (its tables are allocated by pmd_snap_create).  The first call on a device
+ * looks up that device's address of the array (make it before any stream capture).  All
+ * calls on a device share the array: calls whose kernels overlap on the GPU race on it.
+ * Requests whose scratch exceeds the array (about 1 KiB per atom for FP32 forces, 3.7 KiB
+ * with energies; twice that in FP64) return PMD_EUNSUPPORTED. */
+#define PMD_NOALLOC_SCRATCH_BYTES (16u << 20)
+int snap_energy_forces_noalloc(pmd_snap* s, int nbatch, int natoms, const double box[3], const double* pos,
+                               const double* beta, double* energy, double* forces, double* sumB,
+                               pmd_stream_t stream);
+
 /* Finnis-Sinclair EAM energies and forces of nbatch systems (Sec. 3.1), one CTA per system,
  * no scratch.  energy [nbatch] and forces [nbatch][3][natoms] may each be NULL.
  * natoms <= PMD_MAX_COARSE_ATOMS (EUNSUPPORTED otherwise). */

@@ -66,7 +66,7 @@ class Action(ctypes.Structure):
 
 EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_num_coeffs", "pmd_snap_flop_model",
            "pmd_snap_reserve",
-           "snap_energy_forces", "pmd_snap_sync_status", "eam_energy_forces", "pmd_engine_create",
+           "snap_energy_forces", "pmd_snap_sync_status", "snap_energy_forces_noalloc", "eam_energy_forces", "pmd_engine_create",
            "pmd_engine_destroy", "pmd_engine_set_beta", "pmd_engine_reserve", "pmd_engine_profile", "pmd_sync_status",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
            "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log"]
@@ -93,6 +93,7 @@ def lib():
     L.pmd_snap_flop_model.argtypes = [vp, dp, dp]
     L.snap_energy_forces.argtypes = [vp, i32, i32, dp, vp, vp, vp, vp, vp, vp]
     L.pmd_snap_sync_status.argtypes = [vp, vp]
+    L.snap_energy_forces_noalloc.argtypes = [vp, i32, i32, dp, vp, vp, vp, vp, vp, vp]
     L.eam_energy_forces.argtypes = [ctypes.POINTER(FSParams), i32, i32, dp, vp, vp, vp, vp]
     L.pmd_engine_create.argtypes = [ctypes.POINTER(EngineParams), ctypes.POINTER(vp)]
     L.pmd_engine_destroy.argtypes = [vp]

@@ -66,6 +66,16 @@ struct SnapHostTables {
 };
 int build_snap_tables(int twojmax, SnapHostTables* T);
 
+// device scratch of one snap_energy_forces call
+struct SnapScratch {
+    int* nbr;       // [na][PMD_MAX_NEIGHBORS]
+    int* nnb;       // [na]
+    void* dedr;     // [na][PMD_MAX_NEIGHBORS][3] reals
+    float4* qf;     // [na]
+    void* utot;     // [na][nfull] complex reals (energy path)
+    double* B;      // [na][nB] (energy path)
+};
+
 }  // namespace pmd
 
 // ---- contexts -------------------------------------------------------------------------

@@ -378,11 +378,11 @@ __global__ void k_snap_energy(const double* __restrict__ B, int nbatch, int n, i
 
 template <typename real, int TJ>
 static int launch_snap(pmd_snap* s, int nbatch, int n, const double box[3], const double* pos, const double* beta,
-                       double* energy, double* forces, double* sumB, cudaStream_t st) {
+                       double* energy, double* forces, double* sumB, const SnapScratch& sc, cudaStream_t st) {
     const long na = (long)nbatch * n;
     SnapView v = snap_view(s, beta);
     const bool want_B = energy || sumB;
-    float4* qf = s->s_qf.as<float4>();
+    float4* qf = sc.qf;
     if (sizeof(real) == 4) {
         k_wrap_f32<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(pos, nbatch, n, box[0], box[1], box[2], qf);
         PMD_CUDA_TRY(cudaGetLastError());
@@ -393,24 +393,52 @@ static int launch_snap(pmd_snap* s, int nbatch, int n, const double box[3], cons
     long wpb = SNAP_THREADS / 32;
     long blocks = (na + wpb - 1) / wpb;
     k_snap_atoms<real, TJ><<<(unsigned)blocks, SNAP_THREADS, sm, st>>>(
-        v, nbatch, n, box[0], box[1], box[2], pos, qf, s->s_nbr.as<int>(), s->s_nnb.as<int>(), s->s_dedr.as<real>(),
-        want_B ? s->s_utot.as<cplx<real>>() : nullptr, s->s_status.as<int>());
+        v, nbatch, n, box[0], box[1], box[2], pos, qf, sc.nbr, sc.nnb, static_cast<real*>(sc.dedr),
+        want_B ? static_cast<cplx<real>*>(sc.utot) : nullptr, s->s_status.as<int>());
     PMD_CUDA_TRY(cudaGetLastError());
     if (forces) {
         k_snap_gather<real><<<(unsigned)((na + 127) / 128), 128, 0, st>>>(
-            s->s_nbr.as<int>(), s->s_nnb.as<int>(), s->s_dedr.as<real>(), nbatch, n, forces, s->s_status.as<int>());
+            sc.nbr, sc.nnb, static_cast<const real*>(sc.dedr), nbatch, n, forces, s->s_status.as<int>());
         PMD_CUDA_TRY(cudaGetLastError());
     }
     if (want_B) {
         const long nt = na * s->T.nB;
         k_snap_bispectrum<real, TJ><<<(unsigned)((nt + 127) / 128), 128, 0, st>>>(
-            s->s_utot.as<cplx<real>>(), na, s->T.nB, s->d_triblk.as<int4>(), s->d_cg.as<real>(), s->d_blk.as<int4>(),
-            s->s_B.as<double>());
+            static_cast<const cplx<real>*>(sc.utot), na, s->T.nB, s->d_triblk.as<int4>(), s->d_cg.as<real>(),
+            s->d_blk.as<int4>(), sc.B);
         PMD_CUDA_TRY(cudaGetLastError());
-        k_snap_energy<<<nbatch, 64, 0, st>>>(s->s_B.as<double>(), nbatch, n, s->T.nB, beta, energy, sumB);
+        k_snap_energy<<<nbatch, 64, 0, st>>>(sc.B, nbatch, n, s->T.nB, beta, energy, sumB);
         PMD_CUDA_TRY(cudaGetLastError());
     }
     return PMD_OK;
+}
+
+// bytes of each scratch array for na atoms (forces always; U_tot and B only for energies)
+void snap_scratch_sizes(const pmd_snap* s, long na, bool want_B, size_t sz[6]) {
+    const size_t rs = s->p.precision == PMD_FP64 ? 8 : 4;
+    sz[0] = (size_t)na * NMAX * sizeof(int);                          // nbr
+    sz[1] = (size_t)na * sizeof(int);                                 // nnb
+    sz[2] = (size_t)na * NMAX * 3 * rs;                               // dedr
+    sz[3] = (size_t)na * sizeof(float4);                              // qf
+    sz[4] = want_B ? (size_t)na * (size_t)s->T.nfull * 2 * rs : 0;    // utot
+    sz[5] = want_B ? (size_t)na * (size_t)std::max(1, s->T.nB) * sizeof(double) : 0;   // B
+}
+
+int snap_compute_scratch(pmd_snap* s, int nbatch, int n, const double box[3], const double* pos, const double* beta,
+                         double* energy, double* forces, double* sumB, const SnapScratch& sc, cudaStream_t st) {
+    const bool f64 = s->p.precision == PMD_FP64;
+    switch (s->p.twojmax) {
+#define PMD_SNAP_CASE(TJV)                                                                                    \
+    case TJV:                                                                                                 \
+        return f64 ? launch_snap<double, TJV>(s, nbatch, n, box, pos, beta, energy, forces, sumB, sc, st)     \
+                   : launch_snap<float, TJV>(s, nbatch, n, box, pos, beta, energy, forces, sumB, sc, st);
+        PMD_SNAP_CASE(2)
+        PMD_SNAP_CASE(4)
+        PMD_SNAP_CASE(6)
+        PMD_SNAP_CASE(8)
+#undef PMD_SNAP_CASE
+    }
+    return fail(PMD_EUNSUPPORTED, "twojmax must be 2, 4, 6 or 8");
 }
 
 int snap_reserve_impl(pmd_snap* s, long na) {
@@ -429,19 +457,9 @@ int snap_compute(pmd_snap* s, int nbatch, int n, const double box[3], const doub
                  double* energy, double* forces, double* sumB, cudaStream_t st) {
     int rc = snap_reserve_impl(s, (long)nbatch * n);
     if (rc) return rc;
-    const bool f64 = s->p.precision == PMD_FP64;
-    switch (s->p.twojmax) {
-#define PMD_SNAP_CASE(TJV)                                                                                    \
-    case TJV:                                                                                                 \
-        return f64 ? launch_snap<double, TJV>(s, nbatch, n, box, pos, beta, energy, forces, sumB, st)         \
-                   : launch_snap<float, TJV>(s, nbatch, n, box, pos, beta, energy, forces, sumB, st);
-        PMD_SNAP_CASE(2)
-        PMD_SNAP_CASE(4)
-        PMD_SNAP_CASE(6)
-        PMD_SNAP_CASE(8)
-#undef PMD_SNAP_CASE
-    }
-    return fail(PMD_EUNSUPPORTED, "twojmax must be 2, 4, 6 or 8");
+    SnapScratch sc{s->s_nbr.as<int>(), s->s_nnb.as<int>(), s->s_dedr.p, s->s_qf.as<float4>(), s->s_utot.p,
+                   s->s_B.as<double>()};
+    return snap_compute_scratch(s, nbatch, n, box, pos, beta, energy, forces, sumB, sc, st);
 }
 
 }  // namespace pmd
