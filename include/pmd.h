@@ -137,6 +137,7 @@ int pmd_snap_flop_model(const pmd_snap* s, double* per_pair, double* per_atom);
  *   energy [nbatch]             FP64 device or NULL: E = sum_i E_i (eV)
  *   forces [nbatch][3][natoms]  FP64 device or NULL: F = -dE/dq (eV/Angstrom)
  *   sumB   [nbatch][1+nB]       FP64 device or NULL: dE/dbeta (sumB[0] = natoms, sumB[1+t] = sum_i B_t)
+ * With forces == NULL only the U_tot and bispectrum stages run (no adjoint, no dE/dr pass).
  * Stream-ordered; ENEIGH/ENONFINITE surface at pmd_snap_sync_status. */
 int snap_energy_forces(pmd_snap* s, int nbatch, int natoms, const double box[3], const double* pos,
                        const double* beta, double* energy, double* forces, double* sumB,

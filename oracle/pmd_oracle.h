@@ -9,7 +9,7 @@
  * Every routine is a plain, slow, literal statement of what the paper (arXiv
  * 2212.10508) or the method it cites computes, in double precision:
  *   - Langevin scheme: eqs. (2)-(3) (Sec. 2), temperature-corrected form eqs. (11)-(12)
- *     with the schedules (13)-(14) (Sec. 2.4, App. B);
+ *     with the schedules (13)-(14) (Sec. 2.4, App. A.2);
  *   - shared noise G_{l,n}: Sec. 2.1 and 2.3 (same Gaussian increments for F and C and
  *     every parareal iteration), drawn here from Philox4x32-10 + Box-Muller;
  *   - SNAP (Sec. 3.1, cited method of Thompson et al. 2015): bispectrum of the

@@ -265,10 +265,17 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
     if (per_sm < 1) return fail(PMD_EUNSUPPORTED, "persistent SNAP kernel does not fit on an SM");
     const int grid = per_sm * e->num_sms;
     void* args[] = {&a};
-    if (e->profile) PMD_CUDA_TRY(cudaEventRecord(e->ev0, st));
+    // inside a stream capture the timing events must become event nodes of the graph
+    unsigned int ev_flags = cudaEventRecordDefault;
+    if (e->profile) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        PMD_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusActive) ev_flags = cudaEventRecordExternal;
+        PMD_CUDA_TRY(cudaEventRecordWithFlags(e->ev0, st, ev_flags));
+    }
     PMD_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(FINE_THREADS), args, sm, st));
     if (e->profile) {
-        PMD_CUDA_TRY(cudaEventRecord(e->ev1, st));
+        PMD_CUDA_TRY(cudaEventRecordWithFlags(e->ev1, st, ev_flags));
         e->prof_recorded = 1;
     }
     return PMD_OK;

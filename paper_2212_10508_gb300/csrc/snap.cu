@@ -276,7 +276,8 @@ __global__ void __launch_bounds__(SNAP_THREADS) k_snap_atoms(SnapView v, int nba
                                                              double b2, const double* __restrict__ pos,
                                                              const float4* __restrict__ qf, int* __restrict__ nbr,
                                                              int* __restrict__ nnb, real* __restrict__ dedr,
-                                                             cplx<real>* __restrict__ utot, int* status) {
+                                                             cplx<real>* __restrict__ utot, int* status,
+                                                             int want_forces) {
     extern __shared__ __align__(16) unsigned char smem[];
     SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, v);
     snap_shared_load<real, TJ>(sh, v);
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(SNAP_THREADS) k_snap_atoms(SnapView v, int nba
         const int i = (int)(item % n);
         snap_atom_warp2<real, TJ>(sh.ws[warp], v.yt, sh.cg, sh.beff, v.sp, lane, n, i, pos + bb * 3 * n, qf + bb * n,
                                   box, nbr + item * NMAX, nnb + item, dedr + item * NMAX * 3,
-                                  utot ? utot + item * Dims<TJ>::NFULL : nullptr, status);
+                                  utot ? utot + item * Dims<TJ>::NFULL : nullptr, status, want_forces != 0);
     }
 }
 
@@ -394,7 +395,7 @@ static int launch_snap(pmd_snap* s, int nbatch, int n, const double box[3], cons
     long blocks = (na + wpb - 1) / wpb;
     k_snap_atoms<real, TJ><<<(unsigned)blocks, SNAP_THREADS, sm, st>>>(
         v, nbatch, n, box[0], box[1], box[2], pos, qf, sc.nbr, sc.nnb, static_cast<real*>(sc.dedr),
-        want_B ? static_cast<cplx<real>*>(sc.utot) : nullptr, s->s_status.as<int>());
+        want_B ? static_cast<cplx<real>*>(sc.utot) : nullptr, s->s_status.as<int>(), forces != nullptr);
     PMD_CUDA_TRY(cudaGetLastError());
     if (forces) {
         k_snap_gather<real><<<(unsigned)((na + 127) / 128), 128, 0, st>>>(

@@ -434,7 +434,8 @@ template <typename real, int TJ>
 __device__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const SnapV2Tables& yt, const real* __restrict__ cg,
                                 const real* __restrict__ beff, const SnapDevParams& sp, int lane, int n, int i,
                                 const double* q64, const float4* qf, const double box[3], int* nbr_out,
-                                int* nnb_out, real* dedr_out, cplx<real>* utot_out, int* status) {
+                                int* nnb_out, real* dedr_out, cplx<real>* utot_out, int* status,
+                                bool want_forces = true) {
     constexpr int NH = Dims<TJ>::NHALF;
     const real kappa = real(sp.rfac0 * PI / sp.rcut);
     const real rcut = real(sp.rcut);
@@ -453,6 +454,10 @@ __device__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const SnapV2Tables& 
     __syncwarp();
     if (utot_out) {
         for (int e = lane; e < Dims<TJ>::NFULL; e += 32) utot_out[e] = ws.full[e];
+    }
+    if (!want_forces) {   // energies only: the adjoint and force passes are not needed
+        __syncwarp();
+        return;
     }
 
     // Y = sum_blocks beta_eff Z (lockstep rounds, lane-owned outputs)

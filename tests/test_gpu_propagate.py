@@ -112,3 +112,29 @@ def test_noise_is_shared_between_fine_and_coarse_zero_force():
     eng.baoab_propagate_batch(P.COARSE, q2, v2, L, ids, lp)
     eng.sync_status()
     assert torch.equal(q1, q2) and torch.equal(v1, v2)
+
+
+def test_fine_propagation_replays_from_a_cuda_graph():
+    """The whole baoab_propagate_batch(FINE) call (prologue, persistent cooperative kernel) is
+    captured once into a CUDA graph; replays give the direct call's result bit for bit."""
+    q, v, box, beta = _system(4, 6, 1500.0, 18)
+    n = q.shape[2]
+    eng = P.Engine(n, box, P.snap_params(precision=P.FP32_BULK), P.fs_params(), beta=T(W.fitted_beta()))
+    eng.reserve(6)
+    lp = P.langevin(T=1500.0, seed=5)
+    L = T([7, 3, 0, 12, 5, 9], torch.int32)
+    ids = T(np.arange(6), torch.int64)
+    q1, v1 = T(q), T(v)
+    eng.baoab_propagate_batch(P.FINE, q1, v1, L, ids, lp)
+    eng.sync_status()
+    qg, vg = T(q), T(v)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        eng.baoab_propagate_batch(P.FINE, qg, vg, L, ids, lp)
+    for _ in range(2):
+        qg.copy_(T(q))
+        vg.copy_(T(v))
+        g.replay()
+        torch.cuda.synchronize()
+        eng.sync_status()
+        assert torch.equal(qg, q1) and torch.equal(vg, v1)

@@ -1,5 +1,5 @@
 """Pins for the oracle's Langevin schemes: eqs. (2)-(3), the corrected eqs. (11)-(12) with the
-schedules (13)-(14), the closed forms of App. A (V = 0) and App. B, and gamma = 0 physics."""
+schedules (13)-(14), the closed forms of App. A.1 (V = 0) and App. A.2, and gamma = 0 physics."""
 import numpy as np
 import pytest
 
@@ -19,7 +19,7 @@ def _run(q, v, L, n, lp, pot=None, box=np.full(3, 1000.0)):
 
 @pytest.mark.parametrize("schedule", [O.SCHED_NONE, O.SCHED_ROBUST])
 def test_zero_force_closed_form(schedule):
-    """App. A eq. (utile) and its corrected form in App. B: with V = 0, for one noise
+    """App. A.1 (closed form of p_l) and its corrected form in App. A.2: with V = 0, for one noise
     realisation, p_L = mu^2 (1-g dt)^(L-1) p_0 + 2 mu sum_{i=1}^{L-1} (1-g dt)^(i-1) sqrt(th_{L-i}) G_{L-i}
                      + mu sqrt(th_0) (1-g dt)^(L-1) G_0 + sqrt(th_L) G_L,
     and q_L = q_0 + dt sum_l p_{l+1/2} with p_{l+1/2} = (1-g dt)^l p_{1/2} + 2 sum ... ."""
@@ -49,7 +49,7 @@ def test_zero_force_closed_form(schedule):
 
 
 def _exact_stationary_var(L, dt, gamma, kT_m, C):
-    """Fixed point of the finite-dt variance recursion of App. A (uncorrected) / App. B."""
+    """Fixed point of the finite-dt variance recursion of App. A.1 (uncorrected) / App. A.2."""
     mu = 1 - 0.5 * gamma * dt
     r = 1 - gamma * dt
     th = [0.5 * gamma * kT_m * c * dt for c in C]
@@ -64,7 +64,7 @@ def _exact_stationary_var(L, dt, gamma, kT_m, C):
                                               (1, O.SCHED_L1_SYM, 1.0), (4, O.SCHED_NONE, 1 - 1 / 8),
                                               (4, O.SCHED_ROBUST, 1.0)])
 def test_kinetic_temperature_fixed_point(L, schedule, target):
-    """Sec. 2.4 / App. A-B: starting at the exact stationary variance, one interval of L
+    """Sec. 2.4 / App. A: starting at the exact stationary variance, one interval of L
     steps keeps it (empirical, 4 sigma); the stationary value is K_eq = kT/m (1 - 1/(2L)) + O(dt)
     uncorrected and kT/m with the schedules of eqs. (13)-(14) (Tables 5-6)."""
     m = 40000
