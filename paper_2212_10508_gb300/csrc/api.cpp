@@ -244,7 +244,7 @@ int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out) {
 int pmd_engine_destroy(pmd_engine* e) {
     if (!e) return PMD_OK;
     DevBuf* bufs[] = {&e->beta, &e->status, &e->s_nbr, &e->s_nnb, &e->s_dedr, &e->s_qf, &e->s_vh, &e->s_order,
-                      &e->s_result};
+                      &e->s_result, &e->s_noise};
     for (DevBuf* b : bufs) b->release();
     if (e->pinned) cudaFreeHost(e->pinned);
     if (e->ev0) cudaEventDestroy(e->ev0);

@@ -19,6 +19,9 @@ __global__ void __launch_bounds__(512) k_eam_standalone(int n, double b0, double
     s.dF = s.F + 3 * n;
     double* Eat = s.dF + n;
     s.qf = reinterpret_cast<float4*>((reinterpret_cast<size_t>(Eat + n) + 15) / 16 * 16);
+    s.nbl = nullptr;   // one evaluation: scan all atoms
+    s.nbc = nullptr;
+    s.qref = nullptr;
     const double box[3] = {b0, b1, b2};
     const long m = blockIdx.x;
     const double* P = pos + m * 3 * n;

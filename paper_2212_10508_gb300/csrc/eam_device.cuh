@@ -5,7 +5,7 @@
 //   F'(rho) = -A / (2 sqrt rho), 0 when rho = 0.
 // Positions live in shared memory (FP64 rows plus a wrapped FP32 copy used to screen pairs).
 // FP64 mode evaluates every pair term in FP64 from the exact minimum-image displacement;
-// FP32_BULK evaluates pair terms in FP32 and sums in FP64.
+// FP32_BULK evaluates pair terms and per-atom sums in FP32.
 #pragma once
 
 #include "device_common.cuh"
@@ -19,11 +19,21 @@ struct FSDev {
 };
 
 struct EamShared {
-    double* q;    // [3][n]
-    float4* qf;   // [n] wrapped to [0, L)
-    double* F;    // [3][n]
-    double* dF;   // [n]
+    double* q;                 // [3][n]
+    float4* qf;                // [n] wrapped to [0, L)
+    double* F;                 // [3][n]
+    double* dF;                // [n]
+    unsigned short* nbl;       // [n][EAM_LIST_CAP] Verlet list (nullptr: scan all atoms)
+    unsigned char* nbc;        // [n] list lengths
+    float4* qref;              // [n] wrapped positions at the last list build
 };
+
+// Verlet list of the one-CTA coarse path: every pair within max(d, c) + EAM_SKIN, in index
+// order, rebuilt when an atom has moved more than EAM_SKIN / 2 since the last build.  The pair
+// passes re-apply the exact cutoff test, so the list yields the same terms in the same order as
+// a scan over all atoms (bitwise the same sums).
+constexpr int EAM_LIST_CAP = 64;
+constexpr float EAM_SKIN = 0.5f;
 
 __device__ __forceinline__ float4 wrap_f32(double x, double y, double z, const double box[3]) {
     x -= box[0] * floor(x / box[0]);
@@ -64,48 +74,102 @@ __device__ __forceinline__ real pair_geom(const EamShared& s, int n, int i, int 
     }
 }
 
+__device__ __forceinline__ void eam_build_list(const EamShared& s, int n, const double box[3], float reach2,
+                                               int* overflow) {
+    const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 qi = s.qf[i];
+        int c = 0;
+        for (int j = 0; j < n; ++j) {
+            if (j == i || !screen_pair(qi, s.qf[j], boxf, reach2)) continue;
+            if (c < EAM_LIST_CAP) s.nbl[i * EAM_LIST_CAP + c] = (unsigned short)j;
+            ++c;
+        }
+        if (c > EAM_LIST_CAP) atomicOr(overflow, 1);
+        s.nbc[i] = (unsigned char)(c > EAM_LIST_CAP ? EAM_LIST_CAP : c);
+        s.qref[i] = qi;
+    }
+}
+
+// 1 when some atom moved more than half the skin since the list was built (CTA-uniform)
+__device__ __forceinline__ int eam_list_stale(const EamShared& s, int n) {
+    int stale = 0;
+    const float lim2 = 0.25f * EAM_SKIN * EAM_SKIN;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const float4 a = s.qf[i], b = s.qref[i];
+        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+        if (dx * dx + dy * dy + dz * dz > lim2) stale = 1;
+    }
+    return __syncthreads_or(stale);
+}
+
 // Forces into s.F (and per-atom energies into Eat if non-null).  All threads of the CTA call
-// it; it ends with __syncthreads().
+// it; it ends with __syncthreads().  With a list (s.nbl != nullptr) the caller keeps it valid
+// (eam_refresh_list); otherwise every atom is scanned.  FP64 accumulates in double, FP32_BULK in
+// float (pair terms and sums).
 template <typename real>
 __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], const FSDev& p, double* Eat) {
     const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
     const real d_ = (real)p.d, c_ = (real)p.c, c0 = (real)p.c0, c1 = (real)p.c1, c2 = (real)p.c2;
+    const bool list = s.nbl != nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 qi = s.qf[i];
-        double rho = 0.0, ep = 0.0;
-        for (int j = 0; j < n; ++j) {
+        real rho = 0, ep = 0;
+        const int cnt = list ? s.nbc[i] : n;
+        for (int t = 0; t < cnt; ++t) {
+            const int j = list ? s.nbl[i * EAM_LIST_CAP + t] : t;
             if (j == i || !screen_pair(qi, s.qf[j], boxf, p.screen2)) continue;
             real dv[3];
             const real r = pair_geom<real>(s, n, i, j, box, boxf, dv);
-            if (r < d_) rho += (double)((r - d_) * (r - d_));
-            if (r < c_) ep += 0.5 * (double)((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
+            if (r < d_) rho += (r - d_) * (r - d_);
+            if (r < c_) ep += real(0.5) * ((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
         }
-        s.dF[i] = rho > 0.0 ? -p.A / (2.0 * sqrt(rho)) : 0.0;
-        if (Eat) Eat[i] = ep - p.A * sqrt(rho);
+        const double rh = (double)rho;
+        s.dF[i] = rh > 0.0 ? -p.A / (2.0 * sqrt(rh)) : 0.0;
+        if (Eat) Eat[i] = (double)ep - p.A * sqrt(rh);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 qi = s.qf[i];
-        const double dFi = s.dF[i];
-        double f0 = 0.0, f1 = 0.0, f2 = 0.0;
-        for (int j = 0; j < n; ++j) {
+        const real dFi = (real)s.dF[i];
+        real f0 = 0, f1 = 0, f2 = 0;
+        const int cnt = list ? s.nbc[i] : n;
+        for (int t = 0; t < cnt; ++t) {
+            const int j = list ? s.nbl[i * EAM_LIST_CAP + t] : t;
             if (j == i || !screen_pair(qi, s.qf[j], boxf, p.screen2)) continue;
             real dv[3];
             const real r = pair_geom<real>(s, n, i, j, box, boxf, dv);
             real dEdr = real(0);
-            if (r < d_) dEdr += (real)(dFi + s.dF[j]) * real(2) * (r - d_);
+            if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
             if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
             if (r < d_ || r < c_) {
-                f0 += (double)(dEdr * dv[0] / r);
-                f1 += (double)(dEdr * dv[1] / r);
-                f2 += (double)(dEdr * dv[2] / r);
+                f0 += dEdr * dv[0] / r;
+                f1 += dEdr * dv[1] / r;
+                f2 += dEdr * dv[2] / r;
             }
         }
-        s.F[i] = f0;
-        s.F[n + i] = f1;
-        s.F[2 * n + i] = f2;
+        s.F[i] = (double)f0;
+        s.F[n + i] = (double)f1;
+        s.F[2 * n + i] = (double)f2;
     }
     __syncthreads();
+}
+
+// Keep the Verlet list valid for the current positions (rebuild when stale or not built yet).
+__device__ __forceinline__ void eam_refresh_list(const EamShared& s, int n, const double box[3], const FSDev& p,
+                                                 bool force_build, int* status) {
+    if (!s.nbl) return;
+    const int stale = force_build ? 1 : eam_list_stale(s, n);
+    if (stale) {
+        __shared__ int overflow;
+        if (threadIdx.x == 0) overflow = 0;
+        __syncthreads();
+        const float reach = sqrtf(p.screen2) + EAM_SKIN;
+        eam_build_list(s, n, box, reach * reach, &overflow);
+        __syncthreads();
+        if (overflow && threadIdx.x == 0) flag(status, ST_NEIGH);
+        __syncthreads();
+    }
 }
 
 }  // namespace pmd

@@ -101,6 +101,7 @@ struct pmd_engine {
     pmd::DevBuf beta;                // [1+nB] FP64
     pmd::DevBuf status;              // int status word + barrier words
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_vh, s_order, s_Ls, s_result;
+    pmd::DevBuf s_noise;             // Gaussian increments of a parareal_correct window
     int cap_batch = 0;
     int device = 0;
     int num_sms = 0;

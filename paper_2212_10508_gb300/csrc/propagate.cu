@@ -307,8 +307,12 @@ struct OwnState {
     double vh[KMAX][3];
 };
 
+constexpr int EAM_LIST_MAX_ATOMS = 512;   // systems up to this size keep a Verlet list in shared memory
+
 __host__ __device__ inline size_t coarse_smem_bytes(int n) {
-    return (size_t)n * (3 * 8 + 16 + 3 * 8 + 8) + 64;
+    size_t b = (size_t)n * (3 * 8 + 16 + 3 * 8 + 8) + 64;
+    if (n <= EAM_LIST_MAX_ATOMS) b += (size_t)n * (EAM_LIST_CAP * 2 + 1 + 16) + 64;
+    return b;
 }
 
 __device__ inline EamShared coarse_carve(unsigned char* smem, int n) {
@@ -317,33 +321,60 @@ __device__ inline EamShared coarse_carve(unsigned char* smem, int n) {
     s.F = s.q + 3 * n;
     s.dF = s.F + 3 * n;
     s.qf = reinterpret_cast<float4*>(align_up(reinterpret_cast<size_t>(s.dF + n), 16));
+    if (n <= EAM_LIST_MAX_ATOMS) {
+        s.qref = s.qf + n;
+        s.nbl = reinterpret_cast<unsigned short*>(s.qref + n);
+        s.nbc = reinterpret_cast<unsigned char*>(s.nbl + (size_t)n * EAM_LIST_CAP);
+    } else {
+        s.qref = nullptr;
+        s.nbl = nullptr;
+        s.nbc = nullptr;
+    }
     return s;
 }
 
+// G_{l,n} of atom i: from the precomputed window buffer [L+1][3][n] of this interval, or drawn
+template <int KMAX>
+__device__ __forceinline__ void coarse_noise(const LangevinDev& L, const double* Gpre, int64_t nid, int ell, int i,
+                                             int n, double G[3]) {
+    if (Gpre) {
+#pragma unroll
+        for (int al = 0; al < 3; ++al) G[al] = Gpre[((size_t)ell * 3 + al) * n + i];
+    } else {
+        normals3(L.seed, nid, ell, i, G);
+    }
+}
+
 // Runs nsteps sub-steps of interval nid on the CTA-resident state (positions in s.q/s.qf,
-// velocities in own.v).  All threads call it.
+// velocities in own.v).  All threads call it.  list_ok tracks whether the CTA's Verlet list has
+// been built (it persists across intervals of a sweep).
 template <typename real, int KMAX>
 __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int n, const double box[3],
-                                    const FSDev& fs, const LangevinDev& L, int nsteps, int64_t nid, int* status) {
+                                    const FSDev& fs, const LangevinDev& L, int nsteps, int64_t nid, const double* Gpre,
+                                    bool& list_ok, int* status) {
     if (nsteps <= 0) return;
+    eam_refresh_list(s, n, box, fs, !list_ok, status);
+    list_ok = true;
     eam_forces_cta<real>(s, n, box, fs, nullptr);
     bool bad = false;
     if (L.scheme == PMD_SCHEME_PAPER) {
+        double Gc[KMAX][3];
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k)
+        for (int k = 0; k < KMAX; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
 #pragma unroll
             for (int al = 0; al < 3; ++al) own.vh[k][al] = own.v[k][al];
+            if (i < n) coarse_noise<KMAX>(L, Gpre, nid, 0, i, n, Gc[k]);
+        }
         for (int ell = 0; ell < nsteps; ++ell) {
             const double s0 = sched_sigma(L, ell), s1 = sched_sigma(L, ell + 1);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
                 if (i >= n) break;
-                double G[3];
-                normals3(L.seed, nid, ell, i, G);
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
-                    const double vhn = half_kick(L, own.v[k][al], s.F[al * n + i], own.vh[k][al], s0, G[al]);
+                    const double vhn = half_kick(L, own.v[k][al], s.F[al * n + i], own.vh[k][al], s0, Gc[k][al]);
                     own.vh[k][al] = vhn;
                     const double q0 = s.q[al * n + i];
                     const double qn = drift(q0, L.dt, vhn);
@@ -354,16 +385,16 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
             }
             __syncthreads();
+            eam_refresh_list(s, n, box, fs, false, status);
             eam_forces_cta<real>(s, n, box, fs, nullptr);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
                 if (i >= n) break;
-                double G[3];
-                normals3(L.seed, nid, ell + 1, i, G);
+                coarse_noise<KMAX>(L, Gpre, nid, ell + 1, i, n, Gc[k]);   // G_{l+1}: this kick and the next step's
 #pragma unroll
                 for (int al = 0; al < 3; ++al)
-                    own.v[k][al] = half_kick(L, own.vh[k][al], s.F[al * n + i], own.vh[k][al], s1, G[al]);
+                    own.v[k][al] = half_kick(L, own.vh[k][al], s.F[al * n + i], own.vh[k][al], s1, Gc[k][al]);
             }
         }
     } else {
@@ -373,7 +404,7 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 const int i = threadIdx.x + k * blockDim.x;
                 if (i >= n) break;
                 double G[3];
-                normals3(L.seed, nid, ell, i, G);
+                coarse_noise<KMAX>(L, Gpre, nid, ell, i, n, G);
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     double v = kick_b(L, own.v[k][al], s.F[al * n + i]);
@@ -389,6 +420,7 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
             }
             __syncthreads();
+            eam_refresh_list(s, n, box, fs, false, status);
             eam_forces_cta<real>(s, n, box, fs, nullptr);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
@@ -446,7 +478,8 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_coarse_batch(int n, doub
     }
     OwnState<KMAX> own;
     load_state<KMAX>(s, own, n, q + m * stride, v + m * stride, box);
-    coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, Lm, ids[m], status);
+    bool list_ok = false;
+    coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, Lm, ids[m], nullptr, list_ok, status);
     store_state<KMAX>(s, own, n, q + m * stride, v + m * stride);
 }
 
@@ -518,7 +551,7 @@ template <typename real, int KMAX>
 __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, int nsteps, int n_in,
                                  int n_fin, const double* __restrict__ jumps, const double* __restrict__ prev,
                                  double* __restrict__ cur, double* __restrict__ cout, double delta_expl, int metric,
-                                 SweepResult* res, int* status) {
+                                 const double* __restrict__ Gwin, SweepResult* res, int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
     const EamShared s = coarse_carve(smem, n);
     __shared__ double red[33];
@@ -549,9 +582,11 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, do
     }
     double delta = metric == PMD_METRIC_REL ? (den > 0 ? num / den : 0.0) : num;
     int n_stop = n_fin;
+    bool list_ok = false;
     for (int nn = n_in; nn < n_fin; ++nn) {
         const long idx = nn - n_in;
-        coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, nsteps, (int64_t)nn, status);
+        const double* Gp = Gwin ? Gwin + (size_t)idx * (nsteps + 1) * 3 * n : nullptr;
+        coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, nsteps, (int64_t)nn, Gp, list_ok, status);
         __syncthreads();
         double* co = cout + idx * S;
         double* cn = cur + (idx + 1) * S;
@@ -615,6 +650,23 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, do
     }
 }
 
+// G_{l,n} for every interval n of a window, l = 0..L, all atoms: [count][L+1][3][natoms]
+__global__ void k_noise_window(uint64_t seed, int64_t n0, int count, int L1, int natoms, double* __restrict__ G) {
+    const long total = (long)count * L1 * natoms;
+    for (long x = (long)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += (long)gridDim.x * blockDim.x) {
+        const int i = (int)(x % natoms);
+        const long t = x / natoms;
+        const int ell = (int)(t % L1);
+        const long c = t / L1;
+        double g[3];
+        normals3(seed, n0 + c, ell, i, g);
+        double* out = G + ((c * L1 + ell) * 3) * natoms + i;
+        out[0] = g[0];
+        out[natoms] = g[1];
+        out[2 * (long)natoms] = g[2];
+    }
+}
+
 int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, const double* prev, double* cur,
                    double* cout, double delta_expl, int metric, int L, const pmd_langevin& lp, double* delta_host,
                    int* n_stop_host, cudaStream_t st) {
@@ -629,10 +681,23 @@ int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, cons
     const bool f64 = e->p.coarse.precision == PMD_FP64;
     const double* B = e->p.box;
     SweepResult* res = e->s_result.as<SweepResult>();
+    // the window's Gaussian increments, drawn by the whole GPU ahead of the sequential sweep
+    const int count = n_fin - n_in;
+    double* Gwin = nullptr;
+    if (count > 0 && L > 0) {
+        const size_t need = (size_t)count * (L + 1) * 3 * n * sizeof(double);
+        int rc0 = e->s_noise.ensure(need);
+        if (rc0) return rc0;
+        Gwin = e->s_noise.as<double>();
+        const long total = (long)count * (L + 1) * n;
+        const long blocks = std::min<long>((total + 255) / 256, (long)e->num_sms * 16);
+        k_noise_window<<<(unsigned)blocks, 256, 0, st>>>(lp.seed, (int64_t)n_in, count, L + 1, n, Gwin);
+        PMD_CUDA_TRY(cudaGetLastError());
+    }
     auto go = [&](auto kern) -> int {
         PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         kern<<<1, threads, sm, st>>>(n, B[0], B[1], B[2], fs, Ld, L, n_in, n_fin, jumps, prev, cur, cout, delta_expl,
-                                     metric, res, e->status.as<int>());
+                                     metric, Gwin, res, e->status.as<int>());
         PMD_CUDA_TRY(cudaGetLastError());
         return PMD_OK;
     };
