@@ -61,6 +61,10 @@ struct SnapHostTables {
     int nrounds = 0;
     double total_terms = 0;           // Clebsch-Gordan terms per atom (algorithmic, unpadded)
     double padded_terms = 0;          // term slots executed (lockstep padding included)
+    // batched Y phase (FP32, lane = atom): int4 jobs (row, block) grouped by owning warp
+    std::vector<int> sb_jobs;         // [njobs][4]
+    std::vector<int> sb_wptr;         // [twojmax + 1][SB_WARPS + 1] job ranges per stage tb and warp
+    double sb_load_max = 0, sb_load_avg = 0;
     // bispectrum jobs (energy path): per triple t the block id of (j1, j2, j)
     std::vector<int> tri_blk;
 };
@@ -90,6 +94,8 @@ struct pmd_snap {
     pmd::DevBuf d_jobs;      // int4 jobs [nrounds][32]
     pmd::DevBuf d_roundtb;   // uint8 [nrounds]
     pmd::DevBuf d_triblk;    // int4 per triple {blk, ta, tb, tj}
+    pmd::DevBuf d_sbjobs;    // int4 jobs of the batched Y phase
+    pmd::DevBuf d_sbwptr;    // int [twojmax + 1][SB_WARPS + 1]
     // scratch
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_utot, s_B, s_status;
     int cap_atoms = 0;

@@ -22,9 +22,6 @@ namespace pmd {
 SnapView snap_view(const pmd_snap* s, const double* beta);
 int snap_reserve_impl(pmd_snap* s, long na);
 
-#ifndef FINE_THREADS
-#define FINE_THREADS 256
-#endif
 constexpr int COARSE_MAX_THREADS = 512;   // 90 registers per thread: 512 fit the register file
 
 // ---- host-side parameter packing -----------------------------------------------------------
@@ -124,32 +121,45 @@ __device__ __forceinline__ int active_members(const int* Ls, int nbatch, int ell
     return lo;
 }
 
+// Phase B for atom k of member m, one warp: force gather (lanes = neighbour slots), the
+// member's noise G_{ell,n} (lane 0 draws Philox block 0 -> G_x, G_y, lane 1 block 1 -> G_z) and
+// the Langevin update, lane al < 3 advancing component al.
 template <typename real>
-__device__ __forceinline__ void fine_phase_b(const FineArgs& a, int m, int k, int ell) {
+__device__ __noinline__ void fine_phase_b(const FineArgs& a, int m, int k, int ell, int lane) {
     const int n = a.n;
     const int L = a.nsteps[m] < 0 ? 0 : a.nsteps[m];
     double F[3];
-    gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n, (const real*)a.dedr + (long)m * n * NMAX * 3, k,
-                       F, a.status);
+    warp_gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n,
+                            (const real*)a.dedr + (long)m * n * NMAX * 3, k, lane, F, a.status);
     double* Q = a.q + m * a.stride;
     double* V = a.vel + m * a.stride;
     double* VH = a.vh + (long)m * 3 * n;
     const LangevinDev& Lp = a.L;
     const double box[3] = {a.box0, a.box1, a.box2};
-    double G[3];
     const int64_t nid = a.ids[m];
-    bool bad = false;
-    if (Lp.scheme == PMD_SCHEME_PAPER) {
-        normals3(Lp.seed, nid, ell, k, G);
-        const double s = sched_sigma(Lp, ell);
-#pragma unroll
-        for (int al = 0; al < 3; ++al) {
-            const long e = (long)al * n + k;
+    const bool need_noise = Lp.scheme == PMD_SCHEME_PAPER || ell < L;
+    double g0 = 0.0, g1 = 0.0;
+    if (lane < 2 && need_noise) {
+        const uint64_t un = (uint64_t)nid;
+        uint32_t c[4] = {2u * (uint32_t)k + (uint32_t)lane, (uint32_t)ell, (uint32_t)un, (uint32_t)(un >> 32)};
+        philox4x32_10(c, (uint32_t)Lp.seed, (uint32_t)(Lp.seed >> 32));
+        box_muller(c, g0, g1);
+    }
+    const double gx = __shfl_sync(0xffffffffu, g0, 0), gy = __shfl_sync(0xffffffffu, g1, 0);
+    const double gz = __shfl_sync(0xffffffffu, g0, 1);
+    if (lane < 3) {
+        const int al = lane;
+        const double Fa = al == 0 ? F[0] : (al == 1 ? F[1] : F[2]);
+        const double G = al == 0 ? gx : (al == 1 ? gy : gz);
+        const long e = (long)al * n + k;
+        bool bad = false;
+        if (Lp.scheme == PMD_SCHEME_PAPER) {
+            const double s = sched_sigma(Lp, ell);
             double v = V[e];
             double vh = ell == 0 ? v : VH[e];
-            if (ell > 0) v = half_kick(Lp, vh, F[al], vh, s, G[al]);           // finish step ell-1
+            if (ell > 0) v = half_kick(Lp, vh, Fa, vh, s, G);           // finish step ell-1
             if (ell < L) {
-                double vhn = half_kick(Lp, v, F[al], vh, s, G[al]);            // first half of step ell
+                double vhn = half_kick(Lp, v, Fa, vh, s, G);            // first half of step ell
                 double qn = drift(Q[e], Lp.dt, vhn);
                 if (!isfinite(qn)) bad = true;
                 if (fabs(qn - Q[e]) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
@@ -157,20 +167,15 @@ __device__ __forceinline__ void fine_phase_b(const FineArgs& a, int m, int k, in
                 VH[e] = vhn;
             }
             V[e] = v;
-        }
-    } else {
-        if (ell < L) normals3(Lp.seed, nid, ell, k, G);
-#pragma unroll
-        for (int al = 0; al < 3; ++al) {
-            const long e = (long)al * n + k;
+        } else {
             double v = V[e];
-            if (ell > 0) v = kick_b(Lp, v, F[al]);
+            if (ell > 0) v = kick_b(Lp, v, Fa);
             if (ell < L) {
                 double q = Q[e];
                 const double q0 = q;
-                v = kick_b(Lp, v, F[al]);
+                v = kick_b(Lp, v, Fa);
                 q = __dadd_rn(q, __dmul_rn(Lp.hdt, v));
-                v = ou_o(Lp, v, G[al]);
+                v = ou_o(Lp, v, G);
                 q = __dadd_rn(q, __dmul_rn(Lp.hdt, v));
                 if (!isfinite(q)) bad = true;
                 if (fabs(q - q0) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
@@ -178,21 +183,52 @@ __device__ __forceinline__ void fine_phase_b(const FineArgs& a, int m, int k, in
             }
             V[e] = v;
         }
+        if (bad) flag(a.status, ST_NONFINITE);
     }
-    if (bad) flag(a.status, ST_NONFINITE);
-    if (ell < L && sizeof(real) == 4) a.qf[(long)m * n + k] = wrap_f32(Q[k], Q[n + k], Q[2 * n + k], box);
+    __syncwarp();
+    if (lane == 0 && ell < L && sizeof(real) == 4) a.qf[(long)m * n + k] = wrap_f32(Q[k], Q[n + k], Q[2 * n + k], box);
 }
 
-template <typename real, int TJ>
-__global__ void __launch_bounds__(FINE_THREADS) k_fine_persistent(FineArgs a) {
-    extern __shared__ __align__(16) unsigned char smem[];
-    SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, a.v);
-    snap_shared_load<real, TJ>(sh, a.v);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int wpb = blockDim.x >> 5;
-    const long gwarp = (long)blockIdx.x * wpb + warp, nwarps = (long)gridDim.x * wpb;
-    const long gtid = (long)blockIdx.x * blockDim.x + threadIdx.x, nthreads = (long)gridDim.x * blockDim.x;
+// Phase A of sub-step ell over the items (active member, atom) = [0, A n).
+template <typename real, int TJ, class SH>
+__device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, long items, const double box[3]) {
+    const int n = a.n;
+    if constexpr (sizeof(real) == 4) {
+        // batched design: CTA c takes the contiguous item range [c0, c1) in batches of 32 atoms
+        const long chunk = (items + gridDim.x - 1) / gridDim.x;
+        const long c0 = (long)blockIdx.x * chunk;
+        const long c1 = c0 + chunk < items ? c0 + chunk : items;
+        for (long bs = c0; bs < c1; bs += SB_ATOMS) {
+            const int na = (int)(c1 - bs < SB_ATOMS ? c1 - bs : SB_ATOMS);
+            auto at = [&](int slot) {
+                const long it = bs + slot;
+                const long m = a.order[it / n];
+                const int i = (int)(it % n);
+                const long ai = m * n + i;
+                return SBAtom{a.q + m * a.stride, a.qf + m * n, i, a.nbr + ai * NMAX, a.nnb + ai,
+                              (float*)a.dedr + ai * NMAX * 3, nullptr};
+            };
+            sb_batch<TJ>(sh, a.v.sbjobs, a.v.sbwptr, a.v.sp, na, at, n, box, a.status, true);
+        }
+    } else {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int wpb = blockDim.x >> 5;
+        const long gwarp = (long)blockIdx.x * wpb + warp, nwarps = (long)gridDim.x * wpb;
+        for (long it = gwarp; it < items; it += nwarps) {
+            const int m = a.order[it / n];
+            const int i = (int)(it % n);
+            real* dd = (real*)a.dedr + ((long)m * n + i) * NMAX * 3;
+            snap_atom_warp2<real, TJ>(sh.ws[warp], sh.tab, a.v.yt, sh.cg, sh.beff, a.v.sp, lane, n, i, a.q + m * a.stride,
+                                      a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX,
+                                      a.nnb + (long)m * n + i, dd, nullptr, a.status);
+        }
+    }
+}
+
+template <typename real, int TJ, class SH>
+__device__ __forceinline__ void fine_loop(const FineArgs& a, const SH& sh) {
+    const int lane = threadIdx.x & 31;
+    const long gwarp = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = ((long)gridDim.x * blockDim.x) >> 5;
     const int n = a.n;
     const double box[3] = {a.box0, a.box1, a.box2};
     const GridBarrier gb{a.bar, gridDim.x};
@@ -201,21 +237,30 @@ __global__ void __launch_bounds__(FINE_THREADS) k_fine_persistent(FineArgs a) {
         const int A = active_members(a.Ls, a.nbatch, ell);
         if (A == 0) break;
         const long items = (long)A * n;
+        fine_phase_a<real, TJ>(a, sh, items, box);
+        if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
         for (long it = gwarp; it < items; it += nwarps) {
             const int m = a.order[it / n];
-            const int i = (int)(it % n);
-            real* dd = (real*)a.dedr + ((long)m * n + i) * NMAX * 3;
-            snap_atom_warp2<real, TJ>(sh.ws[warp], a.v.yt, sh.cg, sh.beff, a.v.sp, lane, n, i, a.q + m * a.stride,
-                                      a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX,
-                                      a.nnb + (long)m * n + i, dd, nullptr, a.status);
-        }
-        if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
-        for (long it = gtid; it < items; it += nthreads) {
-            const int m = a.order[it / n];
             const int k = (int)(it % n);
-            fine_phase_b<real>(a, m, k, ell);
+            fine_phase_b<real>(a, m, k, ell, lane);
         }
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
+    }
+}
+
+template <typename real, int TJ>
+__global__ void __launch_bounds__(snap_cta_threads<real>(), 1) k_fine_persistent(FineArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    if constexpr (sizeof(real) == 4) {
+        SBShared<TJ> sh = sb_shared_carve<TJ>(smem, a.v);
+        sb_shared_load<TJ>(sh, a.v);
+        __syncthreads();
+        fine_loop<real, TJ>(a, sh);
+    } else {
+        SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, a.v);
+        snap_shared_load<real, TJ>(sh, a.v);
+        __syncthreads();
+        fine_loop<real, TJ>(a, sh);
     }
 }
 
@@ -257,11 +302,12 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
                                                                      a.qf);
         PMD_CUDA_TRY(cudaGetLastError());
     }
-    const size_t sm = snap_shared_bytes<real, TJ>(a.v, FINE_THREADS / 32);
+    constexpr int threads = snap_cta_threads<real>();
+    const size_t sm = sizeof(real) == 4 ? sb_shared_bytes<TJ>(a.v) : snap_shared_bytes<real, TJ>(a.v, threads / 32);
     auto kern = k_fine_persistent<real, TJ>;
     PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0;
-    PMD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, FINE_THREADS, sm));
+    PMD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm));
     if (per_sm < 1) return fail(PMD_EUNSUPPORTED, "persistent SNAP kernel does not fit on an SM");
     const int grid = per_sm * e->num_sms;
     void* args[] = {&a};
@@ -273,7 +319,7 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
         if (cs == cudaStreamCaptureStatusActive) ev_flags = cudaEventRecordExternal;
         PMD_CUDA_TRY(cudaEventRecordWithFlags(e->ev0, st, ev_flags));
     }
-    PMD_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(FINE_THREADS), args, sm, st));
+    PMD_CUDA_TRY(cudaLaunchCooperativeKernel((void*)kern, dim3(grid), dim3(threads), args, sm, st));
     if (e->profile) {
         PMD_CUDA_TRY(cudaEventRecordWithFlags(e->ev1, st, ev_flags));
         e->prof_recorded = 1;

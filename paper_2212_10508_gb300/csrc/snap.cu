@@ -31,6 +31,82 @@ static double clebsch(int tj1, int tm1, int tj2, int tm2, int tJ, int tM) {
     return s;
 }
 
+// Jobs of the batched Y phase (lane = atom).  A job is one output row (tj, p) of the half
+// layout of Y and one block (ta, tb, J = tj); it covers the row's h_ncol(tj) outputs.  The Y
+// phase runs in twojmax + 1 stages, one per sub-block size tb, separated by CTA barriers (so
+// that the CTA executes the unrolled code of one tb at a time).  Within a stage whole rows are
+// assigned to the SB_WARPS warps (longest-processing-time first on a cost model of the FP and
+// load instructions): each output is updated by one warp per stage, in a fixed order, and the
+// stages are ordered by the barriers, so the sums are deterministic.  Each warp's jobs of a stage
+// are ordered by row width.
+static void build_batch_jobs(SnapHostTables* T) {
+    struct RJ {
+        int tj, p, blk, ta, tb;
+        double cost;
+    };
+    const int NTB = T->twojmax + 1;
+    const int nblk = (int)T->blk_ta.size();
+    // per stage tb: rows (tj, p) -> their jobs
+    std::vector<std::map<std::pair<int, int>, std::vector<RJ>>> stage(NTB);
+    for (int tj = 0; tj <= T->twojmax; ++tj) {
+        const int nc = ncol_half(tj);
+        for (int p = 0; p <= tj; ++p)
+            for (int id = 0; id < nblk; ++id) {
+                if (T->blk_tj[id] != tj) continue;
+                const int ta = T->blk_ta[id], tb = T->blk_tb[id];
+                const int s = (ta + tb - tj) / 2, p10 = p + s - tb, c0 = qlo(tj) + s - tb;
+                int ni = 0;
+                for (int i = 0; i <= tb; ++i) ni += (p10 + i >= 0 && p10 + i <= ta);
+                if (!ni) continue;
+                int terms = 0, loads = tb + 1;
+                for (int w = 0; w < tb + nc; ++w) {
+                    if (c0 + w < 0 || c0 + w > ta) continue;
+                    ++loads;
+                    for (int o = 0; o < nc; ++o) terms += (w - o >= 0 && w - o <= tb);
+                }
+                const double cost = ni * (6.0 * terms + 2.0 * loads) + nc * (tb + 1) + 4.0 * nc;
+                stage[tb][{tj, p}].push_back({tj, p, id, ta, tb, cost});
+            }
+    }
+    T->sb_jobs.clear();
+    T->sb_wptr.assign((size_t)NTB * (SB_WARPS + 1), 0);
+    T->sb_load_max = 0.0;
+    T->sb_load_avg = 0.0;
+    for (int tb = 0; tb < NTB; ++tb) {
+        std::vector<std::pair<double, std::pair<int, int>>> rows;
+        for (auto& kv : stage[tb]) {
+            double c = 0.0;
+            for (const RJ& j : kv.second) c += j.cost;
+            rows.push_back({c, kv.first});
+        }
+        std::stable_sort(rows.begin(), rows.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        std::vector<double> load(SB_WARPS, 0.0);
+        std::vector<std::vector<RJ>> wj(SB_WARPS);
+        for (auto& r : rows) {
+            const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            load[w] += r.first;
+            for (const RJ& j : stage[tb][r.second]) wj[w].push_back(j);
+        }
+        int* wp = &T->sb_wptr[(size_t)tb * (SB_WARPS + 1)];
+        wp[0] = (int)T->sb_jobs.size() / 4;
+        for (int w = 0; w < SB_WARPS; ++w) {
+            std::stable_sort(wj[w].begin(), wj[w].end(),
+                             [](const RJ& x, const RJ& y) { return ncol_half(x.tj) < ncol_half(y.tj); });
+            for (const RJ& j : wj[w]) {
+                T->sb_jobs.push_back(j.ta | (j.tb << 4) | (j.tj << 8) | (j.p << 12));
+                T->sb_jobs.push_back(T->blk_cgoff[j.blk]);
+                T->sb_jobs.push_back(uoff_full(j.ta) | (uoff_full(j.tb) << 16));
+                T->sb_jobs.push_back((T->hoff[j.tj] + j.p * ncol_half(j.tj)) | (j.blk << 16));
+            }
+            wp[w + 1] = (int)T->sb_jobs.size() / 4;
+        }
+        double tot = 0.0;
+        for (double x : load) tot += x;
+        T->sb_load_max += *std::max_element(load.begin(), load.end());
+        T->sb_load_avg += tot / SB_WARPS;
+    }
+}
+
 int build_snap_tables(int twojmax, SnapHostTables* T) {
     T->twojmax = twojmax;
     T->tri.clear();
@@ -197,6 +273,7 @@ int build_snap_tables(int twojmax, SnapHostTables* T) {
         }
     }
     T->nrounds = (int)T->round_tb.size();
+    build_batch_jobs(T);
     return PMD_OK;
 }
 
@@ -222,6 +299,10 @@ static int upload_tables(pmd_snap* s) {
     PMD_CUDA_TRY(cudaMemcpy(s->d_jobs.p, T.jobs.data(), T.jobs.size() * sizeof(int), cudaMemcpyHostToDevice));
     if ((rc = s->d_roundtb.ensure(std::max<size_t>(1, T.round_tb.size())))) return rc;
     PMD_CUDA_TRY(cudaMemcpy(s->d_roundtb.p, T.round_tb.data(), T.round_tb.size(), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbjobs.ensure(std::max<size_t>(1, T.sb_jobs.size()) * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbjobs.p, T.sb_jobs.data(), T.sb_jobs.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbwptr.ensure(T.sb_wptr.size() * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbwptr.p, T.sb_wptr.data(), T.sb_wptr.size() * sizeof(int), cudaMemcpyHostToDevice));
     std::vector<int4> tb(T.nB);
     for (int t = 0; t < T.nB; ++t) {
         const int b = T.tri_blk[t];
@@ -245,6 +326,8 @@ SnapView snap_view(const pmd_snap* s, const double* beta) {
     v.yt.jobs = s->d_jobs.as<int4>();
     v.yt.round_tb = s->d_roundtb.as<unsigned char>();
     v.yt.nrounds = s->T.nrounds;
+    v.sbjobs = s->d_sbjobs.as<int4>();
+    v.sbwptr = s->d_sbwptr.as<int>();
     v.beta = beta;
     v.ncg = (int)s->T.cg.size();
     v.nblk = (int)s->T.blk_ta.size();
@@ -272,26 +355,44 @@ __global__ void k_wrap_f32(const double* __restrict__ pos, int nbatch, int n, do
 }
 
 template <typename real, int TJ>
-__global__ void __launch_bounds__(SNAP_THREADS) k_snap_atoms(SnapView v, int nbatch, int n, double b0, double b1,
-                                                             double b2, const double* __restrict__ pos,
-                                                             const float4* __restrict__ qf, int* __restrict__ nbr,
-                                                             int* __restrict__ nnb, real* __restrict__ dedr,
-                                                             cplx<real>* __restrict__ utot, int* status,
-                                                             int want_forces) {
+__global__ void __launch_bounds__(snap_cta_threads<real>(), 1)
+    k_snap_atoms(SnapView v, int nbatch, int n, double b0, double b1, double b2, const double* __restrict__ pos,
+                 const float4* __restrict__ qf, int* __restrict__ nbr, int* __restrict__ nnb, real* __restrict__ dedr,
+                 cplx<real>* __restrict__ utot, int* status, int want_forces) {
     extern __shared__ __align__(16) unsigned char smem[];
-    SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, v);
-    snap_shared_load<real, TJ>(sh, v);
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const double box[3] = {b0, b1, b2};
     const long natoms_all = (long)nbatch * n;
-    const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
-    for (long item = (long)blockIdx.x * (blockDim.x >> 5) + warp; item < natoms_all; item += nwarps) {
-        const long bb = item / n;
-        const int i = (int)(item % n);
-        snap_atom_warp2<real, TJ>(sh.ws[warp], v.yt, sh.cg, sh.beff, v.sp, lane, n, i, pos + bb * 3 * n, qf + bb * n,
-                                  box, nbr + item * NMAX, nnb + item, dedr + item * NMAX * 3,
-                                  utot ? utot + item * Dims<TJ>::NFULL : nullptr, status, want_forces != 0);
+    if constexpr (sizeof(real) == 4) {
+        // batched design: CTA c evaluates the contiguous range of atoms [c0, c1) in batches of 32
+        SBShared<TJ> sh = sb_shared_carve<TJ>(smem, v);
+        sb_shared_load<TJ>(sh, v);
+        __syncthreads();
+        const long chunk = (natoms_all + gridDim.x - 1) / gridDim.x;
+        const long c0 = (long)blockIdx.x * chunk;
+        const long c1 = c0 + chunk < natoms_all ? c0 + chunk : natoms_all;
+        for (long bs = c0; bs < c1; bs += SB_ATOMS) {
+            const int na = (int)(c1 - bs < SB_ATOMS ? c1 - bs : SB_ATOMS);
+            auto at = [&](int slot) {
+                const long item = bs + slot;
+                const long bb = item / n;
+                return SBAtom{pos + bb * 3 * n, qf + bb * n, (int)(item % n), nbr + item * NMAX, nnb + item,
+                              dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr};
+            };
+            sb_batch<TJ>(sh, v.sbjobs, v.sbwptr, v.sp, na, at, n, box, status, want_forces != 0);
+        }
+    } else {
+        SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, v);
+        snap_shared_load<real, TJ>(sh, v);
+        __syncthreads();
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const long nwarps = (long)gridDim.x * (blockDim.x >> 5);
+        for (long item = (long)blockIdx.x * (blockDim.x >> 5) + warp; item < natoms_all; item += nwarps) {
+            const long bb = item / n;
+            const int i = (int)(item % n);
+            snap_atom_warp2<real, TJ>(sh.ws[warp], sh.tab, v.yt, sh.cg, sh.beff, v.sp, lane, n, i, pos + bb * 3 * n,
+                                      qf + bb * n, box, nbr + item * NMAX, nnb + item, dedr + item * NMAX * 3,
+                                      utot ? utot + item * Dims<TJ>::NFULL : nullptr, status, want_forces != 0);
+        }
     }
 }
 
@@ -339,16 +440,15 @@ template <typename real>
 __global__ void k_snap_gather(const int* __restrict__ nbr, const int* __restrict__ nnb,
                               const real* __restrict__ dedr, int nbatch, int n, double* __restrict__ forces,
                               int* status) {
-    const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    // one warp per atom
+    const long idx = ((long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (idx >= (long)nbatch * n) return;
     const long bb = idx / n;
     const int k = (int)(idx % n);
     double F[3];
-    gather_force<real>(nbr + bb * n * NMAX, nnb + bb * n, dedr + bb * n * NMAX * 3, k, F, status);
-    double* out = forces + bb * 3 * n;
-    out[k] = F[0];
-    out[n + k] = F[1];
-    out[2 * n + k] = F[2];
+    warp_gather_force<real>(nbr + bb * n * NMAX, nnb + bb * n, dedr + bb * n * NMAX * 3, k, lane, F, status);
+    if (lane < 3) forces[bb * 3 * n + (long)lane * n + k] = F[lane == 0 ? 0 : (lane == 1 ? 1 : 2)];
 }
 
 // per member: E = sum_i (beta_0 + sum_t beta_t B_it), sumB[t] = sum_i B_it; fixed order.
@@ -388,17 +488,25 @@ static int launch_snap(pmd_snap* s, int nbatch, int n, const double box[3], cons
         k_wrap_f32<<<(unsigned)((na + 255) / 256), 256, 0, st>>>(pos, nbatch, n, box[0], box[1], box[2], qf);
         PMD_CUDA_TRY(cudaGetLastError());
     }
-    const size_t sm = snap_shared_bytes<real, TJ>(v);
-    static_assert(SNAP_THREADS % 32 == 0, "");
+    const bool batched = sizeof(real) == 4;
+    const size_t sm = batched ? sb_shared_bytes<TJ>(v) : snap_shared_bytes<real, TJ>(v);
+    constexpr int threads = snap_cta_threads<real>();
     PMD_CUDA_TRY(cudaFuncSetAttribute(k_snap_atoms<real, TJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    long wpb = SNAP_THREADS / 32;
-    long blocks = (na + wpb - 1) / wpb;
-    k_snap_atoms<real, TJ><<<(unsigned)blocks, SNAP_THREADS, sm, st>>>(
+    long blocks;
+    if (batched) {
+        int dev = 0, nsm = 0;
+        PMD_CUDA_TRY(cudaGetDevice(&dev));
+        PMD_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        blocks = std::min<long>((na + SB_ATOMS - 1) / SB_ATOMS, std::max(1, nsm));
+    } else {
+        blocks = (na + threads / 32 - 1) / (threads / 32);
+    }
+    k_snap_atoms<real, TJ><<<(unsigned)blocks, threads, sm, st>>>(
         v, nbatch, n, box[0], box[1], box[2], pos, qf, sc.nbr, sc.nnb, static_cast<real*>(sc.dedr),
         want_B ? static_cast<cplx<real>*>(sc.utot) : nullptr, s->s_status.as<int>(), forces != nullptr);
     PMD_CUDA_TRY(cudaGetLastError());
     if (forces) {
-        k_snap_gather<real><<<(unsigned)((na + 127) / 128), 128, 0, st>>>(
+        k_snap_gather<real><<<(unsigned)((na + 7) / 8), 256, 0, st>>>(
             sc.nbr, sc.nnb, static_cast<const real*>(sc.dedr), nbatch, n, forces, s->s_status.as<int>());
         PMD_CUDA_TRY(cudaGetLastError());
     }

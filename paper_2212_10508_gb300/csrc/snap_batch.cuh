@@ -1,0 +1,365 @@
+// SNAP per-atom pass, batched design (FP32): a CTA of SB_WARPS warps evaluates SB_ATOMS = 32
+// atoms at a time in three phases separated by CTA barriers.
+//
+//  U phase : warp per atom, lane = neighbour; each lane runs the unrolled half-layout recursion
+//            of U(a_k, b_k) (snap_v2.cuh) and the lanes' weighted values are summed over the 32
+//            lanes in a fixed order.  U_tot of the batch is kept in shared memory as
+//            [element][atom] with a padded leading dimension (SB_LD = 33).
+//  Y phase : lane = atom.  Y^J = sum_blocks beta_eff(J,a,b) Z^J_{ab} on the half layout, in one
+//            stage per sub-block size b (CTA barrier in between: one size's unrolled code at a
+//            time).  In a stage every warp owns whole output rows (J, m') and runs, per block, the
+//            Clebsch-Gordan double sum of the row's outputs: for each row m1' of U^a, the window of U^a columns that
+//            the row's outputs share and one row of U^b are loaded once into registers and
+//            reused by all outputs.  Loop bounds skip out-of-range terms, all control flow and
+//            index arithmetic is warp-uniform, and every lane reads its own atom's element
+//            (stride-1 across lanes: no bank conflicts).
+//  dE/dr   : warp per atom, lane = neighbour: each lane contracts its U(g_k) with three
+//            pre-weighted copies of the atom's Y and finishes dE_i/dr_ik.
+// Every sum runs in a fixed order (no atomics): results are bitwise reproducible.
+#pragma once
+
+#include "snap_v2.cuh"
+
+namespace pmd {
+
+constexpr int SB_ATOMS = 32;              // atoms per batch = lanes of the Y phase
+constexpr int SB_LD = 33;                 // leading dimension of the [element][atom] arrays
+constexpr int SB_WARPS = 16;
+constexpr int SB_THREADS = SB_WARPS * 32;
+constexpr int SB_CHUNK = 8;               // U-pass elements summed per lane-sum round
+
+// Shared memory of one CTA.  Aliases: the U-pass lane buffers live in the Y array (unused
+// during the U phase), the weighted Y copies of the dE/dr phase in the U array (unused after
+// the Y phase).
+template <int TJ>
+struct SBShared {
+    float* cg;                 // Clebsch-Gordan blocks
+    float* beff;               // beta_eff per block
+    ElemRT<float>* tab;        // element table (traversal order)
+    float2* ut;                // [NFULL][SB_LD] U_tot of the batch
+    float2* yt;                // [NHALF][SB_LD] Y of the batch (row-major half index)
+    int* nbr;                  // [SB_ATOMS][NMAX]
+    int* nnb;                  // [SB_ATOMS]
+    Vec4<float>* disp;         // [SB_ATOMS][NMAX]
+    __device__ float2* lv(int warp) const { return yt + warp * SB_CHUNK * SB_LD; }
+    __device__ float2* yw(int warp) const { return ut + warp * 3 * Dims<TJ>::NHALF; }
+};
+
+template <int TJ>
+__host__ __device__ constexpr size_t sb_ut_elems() {
+    const size_t a = (size_t)Dims<TJ>::NFULL * SB_LD, b = (size_t)SB_WARPS * 3 * Dims<TJ>::NHALF;
+    return a > b ? a : b;
+}
+template <int TJ>
+__host__ __device__ constexpr size_t sb_yt_elems() {
+    const size_t a = (size_t)Dims<TJ>::NHALF * SB_LD, b = (size_t)SB_WARPS * SB_CHUNK * SB_LD;
+    return a > b ? a : b;
+}
+
+// ---- U phase -----------------------------------------------------------------------------------
+// Sink of the U recursion: store w * U(g_k) of this lane; every SB_CHUNK elements (traversal
+// order) sum the stored values over the 32 lanes in a fixed order and add them to U_tot.
+template <int TJ>
+struct SinkUB {
+    float2* lv;
+    float2* ut;
+    const ElemRT<float>* tab;
+    int lane, slot;
+    float w;
+    bool first;
+    template <int E>
+    __device__ __forceinline__ void take(cplx<float> v) {
+        constexpr int NH = Dims<TJ>::NHALF;
+        lv[(E % SB_CHUNK) * SB_LD + lane] = make_float2(w * v.re, w * v.im);
+        if constexpr ((E % SB_CHUNK) == SB_CHUNK - 1 || E == NH - 1) {
+            constexpr int base = E - E % SB_CHUNK;
+            constexpr int cnt = E - base + 1;
+            __syncwarp();
+            if (lane < cnt) {
+                float sr = 0.f, si = 0.f;
+#pragma unroll 8
+                for (int j = 0; j < 32; ++j) {
+                    const float2 x = lv[lane * SB_LD + j];
+                    sr += x.x;
+                    si += x.y;
+                }
+                // element base + lane in traversal order; identity on the diagonal (self term)
+                const ElemRT<float>& t = tab[base + lane];
+                float2* d = ut + t.full * SB_LD + slot;
+                if (first) {
+                    *d = make_float2(sr + (t.diag ? 1.f : 0.f), si);
+                } else {
+                    const float2 o = *d;
+                    *d = make_float2(o.x + sr, o.y + si);
+                }
+            }
+            __syncwarp();
+        }
+    }
+};
+
+template <int TJ>
+__device__ __noinline__ void sb_u_round(float2* lv, float2* ut, const Vec4<float>* disp, const ElemRT<float>* tab,
+                                        int lane, int slot, int k, int cnt, float kappa, float rcut, int sw,
+                                        bool first) {
+    cplx<float> a{1.f, 0.f}, b{0.f, 0.f};
+    float w = 0.f;
+    if (k < cnt) cayley_klein<float>(disp[k], kappa, rcut, sw, a, b, w);
+    SinkUB<TJ> sink{lv, ut, tab, lane, slot, w, first};
+    URec<float, TJ, SinkUB<TJ>> rec(a, b, sink);
+    ForE<0, Dims<TJ>::NHALF>::run(rec);
+}
+
+// ---- Y phase -----------------------------------------------------------------------------------
+// One job: output row (tj, p) of the half layout (NC = h_ncol(tj) outputs, columns q = qlo..tj)
+// and one block (ta, tb = TB, J = tj), s = (ta + tb - tj)/2.  Output (p, q) sums over rows
+// p1 = p + s - TB + i of U^a (i = 0..TB, p2 = TB - i) and columns q1 = q + s - TB + k of U^a
+// (k = 0..TB, q2 = TB - k):  C(p1, p2) C(q1, q2) U^a[p1][q1] U^b[p2][q2].  With the window
+// slot w = q1 - (qlo + s - TB), output o = q - qlo uses slot w = o + k.
+// Job record: x = ta | tb << 4 | tj << 8 | p << 12; y = CG offset of the block;
+// z = full offset of U^a | full offset of U^b << 16; w = half index of (tj, p, qlo) | blk << 16.
+template <int TB, int NC>
+__device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__ ut, const float* __restrict__ cg,
+                                        const float* __restrict__ beff, float2* __restrict__ yt, int lane) {
+    const int ta = J.x & 15, tj = (J.x >> 8) & 15, p = (J.x >> 12) & 15;
+    const int s = (ta + TB - tj) >> 1;
+    const int p10 = p + s - TB;
+    const int c0 = ((tj + 1) >> 1) + s - TB;
+    const float* c = cg + J.y;
+    float c2[NC][TB + 1];
+#pragma unroll
+    for (int o = 0; o < NC; ++o)
+#pragma unroll
+        for (int k = 0; k <= TB; ++k) {
+            const int q1 = c0 + o + k;
+            const bool ok = q1 >= 0 && q1 <= ta;
+            c2[o][k] = ok ? c[(ok ? q1 : 0) * (TB + 1) + (TB - k)] : 0.f;
+        }
+    const int ilo = p10 < 0 ? -p10 : 0;
+    const int ihi = ta - p10 < TB ? ta - p10 : TB;
+    const int wlo = c0 < 0 ? -c0 : 0, whi = ta - c0;
+    const int ua = J.z & 0xffff, ub = J.z >> 16;
+    float zr[NC], zi[NC];
+#pragma unroll
+    for (int o = 0; o < NC; ++o) zr[o] = zi[o] = 0.f;
+    for (int i = ilo; i <= ihi; ++i) {
+        const int p1 = p10 + i;
+        const float c1 = c[p1 * (TB + 1) + (TB - i)];
+        const float2* yb = ut + (ub + (TB - i) * (TB + 1)) * SB_LD + lane;
+        float2 y[TB + 1];
+#pragma unroll
+        for (int k = 0; k <= TB; ++k) y[k] = yb[(TB - k) * SB_LD];
+        const int xrow = ua + p1 * (ta + 1) + c0;   // window slot 0 (only valid slots are read)
+        float tr[NC], ti[NC];
+#pragma unroll
+        for (int o = 0; o < NC; ++o) tr[o] = ti[o] = 0.f;
+#pragma unroll
+        for (int w = 0; w < TB + NC; ++w) {
+            if (w < wlo || w > whi) continue;
+            const float2 x = ut[(xrow + w) * SB_LD + lane];
+#pragma unroll
+            for (int o = 0; o < NC; ++o) {
+                const int k = w - o;
+                if (k < 0 || k > TB) continue;
+                const float pr = x.x * y[k].x - x.y * y[k].y;
+                const float pi = x.x * y[k].y + x.y * y[k].x;
+                tr[o] += c2[o][k] * pr;
+                ti[o] += c2[o][k] * pi;
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < NC; ++o) {
+            zr[o] += c1 * tr[o];
+            zi[o] += c1 * ti[o];
+        }
+    }
+    const float be = beff[J.w >> 16];
+    float2* out = yt + (J.w & 0xffff) * SB_LD + lane;
+#pragma unroll
+    for (int o = 0; o < NC; ++o) {
+        const float2 v = out[o * SB_LD];
+        out[o * SB_LD] = make_float2(v.x + be * zr[o], v.y + be * zi[o]);
+    }
+}
+
+template <int TJ>
+__device__ __noinline__ void sb_y_phase(const int4* __restrict__ jobs, int j0, int j1, const float2* ut,
+                                        const float* cg, const float* beff, float2* yt, int lane) {
+    for (int j = j0; j < j1; ++j) {
+        const int4 J = jobs[j];
+        const int tb = (J.x >> 4) & 15, tj = (J.x >> 8) & 15;
+        const int nc = tj + 1 - ((tj + 1) >> 1);
+        switch (nc * 16 + tb) {
+#define PMD_SB_CASE(NC_, TB_)                                                         \
+    case NC_ * 16 + TB_:                                                              \
+        if constexpr (TB_ <= TJ && NC_ <= h_ncol(TJ)) sb_yjob<TB_, NC_>(J, ut, cg, beff, yt, lane); \
+        break;
+#define PMD_SB_ROW(NC_)                                                                          \
+    PMD_SB_CASE(NC_, 0) PMD_SB_CASE(NC_, 1) PMD_SB_CASE(NC_, 2) PMD_SB_CASE(NC_, 3)              \
+    PMD_SB_CASE(NC_, 4) PMD_SB_CASE(NC_, 5) PMD_SB_CASE(NC_, 6) PMD_SB_CASE(NC_, 7) PMD_SB_CASE(NC_, 8)
+            PMD_SB_ROW(1)
+            PMD_SB_ROW(2)
+            PMD_SB_ROW(3)
+            PMD_SB_ROW(4)
+            PMD_SB_ROW(5)
+#undef PMD_SB_ROW
+#undef PMD_SB_CASE
+            default: break;
+        }
+    }
+}
+
+// ---- dE/dr phase -------------------------------------------------------------------------------
+// yw[0..2][E] (traversal order) = wS Y(p,q), wP Y(p,q+1), wQ Y(p,q-1) of the atom in slot.
+template <int TJ>
+__device__ __forceinline__ void sb_weight_y(const float2* yt, int slot, float2* yw, const ElemRT<float>* tab,
+                                            int lane) {
+    constexpr int NH = Dims<TJ>::NHALF;
+    for (int e = lane; e < NH; e += 32) {
+        const ElemRT<float>& t = tab[e];
+        const float2 y0 = yt[t.hidx * SB_LD + slot];
+        float2 yp = make_float2(0.f, 0.f), ym = make_float2(0.f, 0.f);
+        if (t.ypH >= 0) yp = yt[t.ypH * SB_LD + slot];
+        if (t.ymH >= 0) {
+            ym = yt[t.ymH * SB_LD + slot];
+            if (t.ymMode != 0) ym = make_float2(t.ymMode * ym.x, -t.ymMode * ym.y);
+        }
+        yw[e] = make_float2(t.wS * y0.x, t.wS * y0.y);
+        yw[NH + e] = make_float2(t.wP * yp.x, t.wP * yp.y);
+        yw[2 * NH + e] = make_float2(t.wQ * ym.x, t.wQ * ym.y);
+    }
+}
+
+template <int TJ>
+struct SinkFB {
+    const float2* yw;
+    float Dim = 0.f, Sre = 0.f, Pre = 0.f, Pim = 0.f, Qre = 0.f, Qim = 0.f;
+    template <int E>
+    __device__ __forceinline__ void take(cplx<float> u) {
+        constexpr HM m = hm(E);
+        constexpr int NH = Dims<TJ>::NHALF;
+        const float2 y = yw[E];
+        Sre += y.x * u.re + y.y * u.im;
+        if constexpr (m.wD != 0.0) {
+            constexpr float r = float(m.wD / m.wS);
+            Dim += r * (y.x * u.im - y.y * u.re);
+        }
+        if constexpr (m.yp >= 0) {
+            const float2 yp = yw[NH + E];
+            Pre += yp.x * u.re + yp.y * u.im;
+            Pim += yp.x * u.im - yp.y * u.re;
+        }
+        if constexpr (m.ym >= 0) {
+            const float2 ym = yw[2 * NH + E];
+            Qre += ym.x * u.re + ym.y * u.im;
+            Qim += ym.x * u.im - ym.y * u.re;
+        }
+    }
+};
+
+template <int TJ>
+__device__ __noinline__ void sb_f_round(const float2* yw, const Vec4<float>* disp, int k, int cnt, float kappa,
+                                        float rcut, int sw, float* dedr_out) {
+    cplx<float> a{1.f, 0.f}, b{0.f, 0.f};
+    float w = 0.f;
+    const Vec4<float> d = disp[k < cnt ? k : 0];
+    if (k < cnt) cayley_klein<float>(d, kappa, rcut, sw, a, b, w);
+    SinkFB<TJ> sink{yw};
+    URec<float, TJ, SinkFB<TJ>> rec(a, b, sink);
+    ForE<0, Dims<TJ>::NHALF>::run(rec);
+    if (k < cnt) {
+        float out[3];
+        dedr_lane<float>(d, kappa, rcut, sw, a, b, w, sink.Dim, sink.Sre, sink.Pre, sink.Pim, sink.Qre, sink.Qim, out);
+        dedr_out[k * 3 + 0] = out[0];
+        dedr_out[k * 3 + 1] = out[1];
+        dedr_out[k * 3 + 2] = out[2];
+    }
+}
+
+// ---- one batch ---------------------------------------------------------------------------------
+// Where atom `slot` of the batch lives and where its results go.
+struct SBAtom {
+    const double* q64;     // member positions [3][n]
+    const float4* qf;      // member positions wrapped to FP32 [n]
+    int i;                 // atom index in its member
+    int* nbr_out;          // [NMAX]
+    int* nnb_out;
+    float* dedr_out;       // [NMAX][3]
+    cplx<float>* utot_out; // [NFULL] or nullptr
+};
+
+// All threads of the CTA call it with the same arguments.  at(slot) returns the SBAtom of the
+// batch's atom slot (slot < na).  Ends with a CTA barrier.
+template <int TJ, class AtomOf>
+__device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, const int* __restrict__ wptr,
+                         const SnapDevParams& sp, int na, const AtomOf& at, int n, const double box[3], int* status,
+                         bool want_forces) {
+    constexpr int NH = Dims<TJ>::NHALF, NF = Dims<TJ>::NFULL;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float kappa = float(sp.rfac0 * PI / sp.rcut);
+    const float rcut = float(sp.rcut);
+
+    // U phase
+    for (int slot = warp; slot < SB_ATOMS; slot += SB_WARPS) {
+        if (slot >= na) {   // empty slot: a zero column keeps the Y phase finite
+            for (int f = lane; f < NF; f += 32) sh.ut[f * SB_LD + slot] = make_float2(0.f, 0.f);
+            continue;
+        }
+        const SBAtom A = at(slot);
+        int* nb = sh.nbr + slot * NMAX;
+        Vec4<float>* dp = sh.disp + slot * NMAX;
+        const int cnt = warp_neighbors<float>(nb, dp, lane, n, A.i, A.q64, A.qf, box, sp.rcut, status);
+        for (int s = lane; s < cnt; s += 32) A.nbr_out[s] = nb[s];
+        if (lane == 0) {
+            *A.nnb_out = cnt;
+            sh.nnb[slot] = cnt;
+        }
+        const int nround = (cnt + 31) / 32;
+        float2* lv = sh.lv(warp);
+        for (int r = 0; r < (nround > 0 ? nround : 1); ++r)
+            sb_u_round<TJ>(lv, sh.ut, dp, sh.tab, lane, slot, r * 32 + lane, cnt, kappa, rcut, sp.switchflag, r == 0);
+        for (int e = lane; e < NH; e += 32) {
+            const ElemRT<float>& t = sh.tab[e];
+            if (t.mir >= 0) {
+                const float2 v = sh.ut[t.full * SB_LD + slot];
+                const float sg = t.mirneg ? -1.f : 1.f;
+                sh.ut[t.mir * SB_LD + slot] = make_float2(sg * v.x, -sg * v.y);
+            }
+        }
+        __syncwarp();
+        if (A.utot_out) {
+            for (int f = lane; f < NF; f += 32) {
+                const float2 v = sh.ut[f * SB_LD + slot];
+                A.utot_out[f] = cplx<float>{v.x, v.y};
+            }
+        }
+    }
+    __syncthreads();
+    if (!want_forces) return;
+
+    // Y phase
+    for (int x = threadIdx.x; x < NH * SB_LD; x += blockDim.x) sh.yt[x] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int tb = 0; tb <= TJ; ++tb) {   // one stage per sub-block size
+        const int* wp = wptr + tb * (SB_WARPS + 1);
+        if (wp[0] == wp[SB_WARPS]) continue;
+        sb_y_phase<TJ>(jobs, wp[warp], wp[warp + 1], sh.ut, sh.cg, sh.beff, sh.yt, lane);
+        __syncthreads();
+    }
+
+    // dE/dr phase
+    for (int slot = warp; slot < na; slot += SB_WARPS) {
+        const SBAtom A = at(slot);
+        float2* yw = sh.yw(warp);
+        sb_weight_y<TJ>(sh.yt, slot, yw, sh.tab, lane);
+        __syncwarp();
+        const int cnt = sh.nnb[slot];
+        const Vec4<float>* dp = sh.disp + slot * NMAX;
+        for (int r = 0; r * 32 < cnt; ++r)
+            sb_f_round<TJ>(yw, dp, r * 32 + lane, cnt, kappa, rcut, sp.switchflag, A.dedr_out);
+        __syncwarp();
+    }
+    __syncthreads();
+}
+
+}  // namespace pmd

@@ -149,23 +149,27 @@ __device__ __forceinline__ void cayley_klein(const Vec4<real>& d, real kappa, re
     }
 }
 
-// Force on atom k of a system: F_k = sum_{j in N(k)} (dE_k/dr_kj - dE_j/dr_jk), neighbour lists
-// sorted by index and symmetric; the slot of k in N(j) is found by binary search.
+// Force on atom k of a system, one warp: F_k = sum_{j in N(k)} (dE_k/dr_kj - dE_j/dr_jk), with
+// neighbour lists sorted by index and symmetric.  Lane l handles the neighbour slots l and l + 32
+// of N(k) and finds the slot of k in N(j) by binary search (the searches of the lanes overlap);
+// the per-lane partial sums are combined by a butterfly over the 32 lanes: a fixed order, and
+// every lane ends with the same bits.
 template <typename real>
-__device__ __forceinline__ void gather_force(const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                             const real* __restrict__ dedr, int k, double F[3], int* status) {
-    F[0] = F[1] = F[2] = 0.0;
+__device__ __forceinline__ void warp_gather_force(const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                  const real* __restrict__ dedr, int k, int lane, double F[3],
+                                                  int* status) {
     const int ck = nnb[k];
     const int* lk = nbr + (size_t)k * NMAX;
     const real* dk = dedr + (size_t)k * NMAX * 3;
-    for (int s = 0; s < ck; ++s) {
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int s = lane; s < ck; s += 32) {
         const int j = lk[s];
         const int cj = nnb[j];
         const int* lj = nbr + (size_t)j * NMAX;
         int lo = 0, hi = cj - 1, t = -1;
         while (lo <= hi) {
-            int mid = (lo + hi) >> 1;
-            int v = lj[mid];
+            const int mid = (lo + hi) >> 1;
+            const int v = lj[mid];
             if (v == k) {
                 t = mid;
                 break;
@@ -173,15 +177,22 @@ __device__ __forceinline__ void gather_force(const int* __restrict__ nbr, const 
             if (v < k) lo = mid + 1;
             else hi = mid - 1;
         }
-        const real* dj = dedr + ((size_t)j * NMAX + (t < 0 ? 0 : t)) * 3;
         if (t < 0) flag(status, ST_BADNEIGH);
+        const real* dj = dedr + ((size_t)j * NMAX + (t < 0 ? 0 : t)) * 3;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            double g = (double)dk[s * 3 + a];
-            double h = t < 0 ? 0.0 : (double)dj[a];
-            F[a] += g - h;
+            const double g = (double)dk[s * 3 + a];
+            const double h = t < 0 ? 0.0 : (double)dj[a];
+            f[a] += g - h;
         }
     }
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[a] += __shfl_xor_sync(0xffffffffu, f[a], m);
+    F[0] = f[0];
+    F[1] = f[1];
+    F[2] = f[2];
 }
 
 }  // namespace pmd

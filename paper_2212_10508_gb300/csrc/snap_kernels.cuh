@@ -2,7 +2,7 @@
 // followed by one WarpScratch2 per warp.
 #pragma once
 
-#include "snap_v2.cuh"
+#include "snap_batch.cuh"
 
 namespace pmd {
 
@@ -16,6 +16,8 @@ struct SnapView {
     const int* befft;
     const double* beffc;
     SnapV2Tables yt;
+    const int4* sbjobs;      // batched Y phase jobs (FP32 design)
+    const int* sbwptr;       // [twojmax + 1][SB_WARPS + 1] job ranges per stage and warp
     const double* beta;
     int ncg, nblk, nB;
     SnapDevParams sp;
@@ -25,6 +27,7 @@ template <typename real, int TJ>
 struct SnapShared {
     real* cg;
     real* beff;
+    ElemRT<real>* tab;
     WarpScratch2<real, TJ>* ws;
 };
 
@@ -35,6 +38,7 @@ __host__ __device__ inline size_t snap_table_bytes(const SnapView& v) {
     size_t o = 0;
     o = align_up(o + (size_t)v.ncg * sizeof(real), 32);
     o = align_up(o + (size_t)v.nblk * sizeof(real), 32);
+    o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<real>), 32);
     return o;
 }
 
@@ -51,6 +55,8 @@ __device__ inline SnapShared<real, TJ> snap_shared_carve(unsigned char* smem, co
     o = align_up(o + (size_t)v.ncg * sizeof(real), 32);
     sh.beff = reinterpret_cast<real*>(smem + o);
     o = align_up(o + (size_t)v.nblk * sizeof(real), 32);
+    sh.tab = reinterpret_cast<ElemRT<real>*>(smem + o);
+    o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<real>), 32);
     sh.ws = reinterpret_cast<WarpScratch2<real, TJ>*>(smem + o);
     return sh;
 }
@@ -66,6 +72,62 @@ __device__ inline void snap_shared_load(SnapShared<real, TJ>& sh, const SnapView
         for (int c = v.beffptr[b]; c < v.beffptr[b + 1]; ++c) s += v.beffc[c] * v.beta[1 + v.befft[c]];
         sh.beff[b] = (real)s;
     }
+    fill_elem_table<real, TJ>(sh.tab);
+}
+
+// ---- batched FP32 design (snap_batch.cuh) ----------------------------------------------------
+template <int TJ>
+__host__ __device__ inline size_t sb_shared_bytes(const SnapView& v) {
+    size_t o = 0;
+    o = align_up(o + (size_t)v.ncg * sizeof(float), 32);
+    o = align_up(o + (size_t)v.nblk * sizeof(float), 32);
+    o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<float>), 32);
+    o = align_up(o + sb_ut_elems<TJ>() * sizeof(float2), 32);
+    o = align_up(o + sb_yt_elems<TJ>() * sizeof(float2), 32);
+    o = align_up(o + (size_t)SB_ATOMS * NMAX * sizeof(int), 32);
+    o = align_up(o + (size_t)SB_ATOMS * sizeof(int), 32);
+    o = align_up(o + (size_t)SB_ATOMS * NMAX * sizeof(Vec4<float>), 32);
+    return o;
+}
+
+template <int TJ>
+__device__ inline SBShared<TJ> sb_shared_carve(unsigned char* smem, const SnapView& v) {
+    SBShared<TJ> sh;
+    size_t o = 0;
+    sh.cg = reinterpret_cast<float*>(smem + o);
+    o = align_up(o + (size_t)v.ncg * sizeof(float), 32);
+    sh.beff = reinterpret_cast<float*>(smem + o);
+    o = align_up(o + (size_t)v.nblk * sizeof(float), 32);
+    sh.tab = reinterpret_cast<ElemRT<float>*>(smem + o);
+    o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<float>), 32);
+    sh.ut = reinterpret_cast<float2*>(smem + o);
+    o = align_up(o + sb_ut_elems<TJ>() * sizeof(float2), 32);
+    sh.yt = reinterpret_cast<float2*>(smem + o);
+    o = align_up(o + sb_yt_elems<TJ>() * sizeof(float2), 32);
+    sh.nbr = reinterpret_cast<int*>(smem + o);
+    o = align_up(o + (size_t)SB_ATOMS * NMAX * sizeof(int), 32);
+    sh.nnb = reinterpret_cast<int*>(smem + o);
+    o = align_up(o + (size_t)SB_ATOMS * sizeof(int), 32);
+    sh.disp = reinterpret_cast<Vec4<float>*>(smem + o);
+    return sh;
+}
+
+template <int TJ>
+__device__ inline void sb_shared_load(SBShared<TJ>& sh, const SnapView& v) {
+    const float* cg = reinterpret_cast<const float*>(v.cg);
+    for (int x = threadIdx.x; x < v.ncg; x += blockDim.x) sh.cg[x] = cg[x];
+    for (int b = threadIdx.x; b < v.nblk; b += blockDim.x) {
+        double s = 0.0;
+        for (int c = v.beffptr[b]; c < v.beffptr[b + 1]; ++c) s += v.beffc[c] * v.beta[1 + v.befft[c]];
+        sh.beff[b] = (float)s;
+    }
+    fill_elem_table<float, TJ>(sh.tab);
+}
+
+// threads per CTA of the SNAP kernels: the batched FP32 design or one warp per atom (FP64)
+template <typename real>
+__host__ __device__ constexpr int snap_cta_threads() {
+    return sizeof(real) == 4 ? SB_THREADS : SNAP_THREADS;
 }
 
 }  // namespace pmd

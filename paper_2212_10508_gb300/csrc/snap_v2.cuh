@@ -146,6 +146,37 @@ struct URec {
     }
 };
 
+// per-element data used by lane-strided runtime loops (one table per CTA, in shared memory)
+// ypH / ymH: half (row-major) index holding Y(p, q+1) / Y(p, q-1), -1 when the weight is zero;
+// ymMode: 0 when Y(p, q-1) is stored directly, +-1 when it is the mirror image
+// Y(p, q-1) = ymMode * conj(Y(tj-p, tj-q+1)) of a stored element.
+template <typename real>
+struct ElemRT {
+    int full, mir, hidx, yp, ym, mirneg, diag;
+    int ypH, ymH, ymMode;
+    real wD, wP, wQ, wS;
+};
+
+template <typename real, int TJ>
+__device__ inline void fill_elem_table(ElemRT<real>* tab) {
+    for (int e = threadIdx.x; e < Dims<TJ>::NHALF; e += blockDim.x) {
+        const HM m = hm(e);
+        const int nc = h_ncol(m.tj), ql = h_qlo(m.tj);
+        const int ypH = m.yp >= 0 ? m.hidx + 1 : -1;
+        int ymH = -1, ymMode = 0;
+        if (m.ym >= 0) {
+            if (m.q - 1 >= ql) {
+                ymH = m.hidx - 1;
+            } else {
+                ymH = h_off(m.tj) + (m.tj - m.p) * nc + (m.tj - m.q + 1 - ql);
+                ymMode = ((m.p - m.q + 1) & 1) ? -1 : 1;
+            }
+        }
+        tab[e] = ElemRT<real>{m.full, m.mir, m.hidx, m.yp, m.ym, m.mirneg, m.p == m.q ? 1 : 0, ypH, ymH, ymMode,
+                              real(m.wD), real(m.wP), real(m.wQ), real(m.wS)};
+    }
+}
+
 // per-warp shared memory of the second design
 template <typename real, int TJ>
 struct WarpScratch2 {
@@ -153,26 +184,27 @@ struct WarpScratch2 {
     Vec4<real> disp[NMAX];
     cplx<real> full[Dims<TJ>::NFULL];                      // U_tot, then Y
     union {
-        cplx<real> lv[32 * 33];                            // lane values of 32 elements (U pass)
+        cplx<real> lv[16 * 33];                            // lane values of 16 elements (U pass)
         cplx<real> yh[Dims<TJ>::NHALF + 1];                // Y half accumulators (Y pass), +1 dummy
         cplx<real> yw[4 * Dims<TJ>::NHALF];                // weighted Y copies (dE/dr pass)
     };
 };
 
-// U pass sink: store w * U(g_k) of this lane; every 32 elements (traversal order) sum the
+// U pass sink: store w * U(g_k) of this lane; every 16 elements (traversal order) sum the
 // stored values over the 32 lanes in a fixed order and add them to U_tot.
 template <typename real, int TJ>
 struct SinkU {
     WarpScratch2<real, TJ>& ws;
+    const ElemRT<real>* tab;
     int lane;
     real w;
     bool first;
     template <int E>
     __device__ __forceinline__ void take(cplx<real> v) {
         constexpr int NH = Dims<TJ>::NHALF;
-        ws.lv[(E & 31) * 33 + lane] = {w * v.re, w * v.im};
-        if constexpr ((E & 31) == 31 || E == NH - 1) {
-            constexpr int base = E & ~31;
+        ws.lv[(E & 15) * 33 + lane] = {w * v.re, w * v.im};
+        if constexpr ((E & 15) == 15 || E == NH - 1) {
+            constexpr int base = E & ~15;
             constexpr int cnt = E - base + 1;
             __syncwarp();
             if (lane < cnt) {
@@ -183,15 +215,11 @@ struct SinkU {
                     sr += x.re;
                     si += x.im;
                 }
-                // element base + lane in traversal order
-                const int e = base + lane;
-                int tj = 0;
-                while (e >= h_off(tj + 1)) ++tj;
-                const int loc = e - h_off(tj);
-                const int p = loc % (tj + 1), q = h_qlo(tj) + loc / (tj + 1);
-                const int f = f_off(tj) + p * (tj + 1) + q;
+                // element base + lane in traversal order; identity on the diagonal (self term)
+                const ElemRT<real>& t = tab[base + lane];
+                const int f = t.full;
                 if (first) {
-                    ws.full[f] = {sr + (p == q ? real(1) : real(0)), si};
+                    ws.full[f] = {sr + (t.diag ? real(1) : real(0)), si};
                 } else {
                     ws.full[f].re += sr;
                     ws.full[f].im += si;
@@ -283,7 +311,7 @@ __device__ __forceinline__ void y_job(const int4 J, const cplx<real>* __restrict
 }
 
 template <typename real>
-__device__ __forceinline__ void y_rounds(const int4* __restrict__ jobs, const unsigned char* __restrict__ round_tb,
+__device__ __noinline__ void y_rounds(const int4* __restrict__ jobs, const unsigned char* __restrict__ round_tb,
                                          int nrounds, int lane, const cplx<real>* U, const real* cg, const real* beff,
                                          cplx<real>* yh) {
     for (int r = 0; r < nrounds; ++r) {
@@ -302,63 +330,47 @@ __device__ __forceinline__ void y_rounds(const int4* __restrict__ jobs, const un
     }
 }
 
-// ---- mirror / expansion helpers ----------------------------------------------------------------
+// ---- mirror / expansion helpers (lane-strided loops over the element table) -------------------
 template <typename real, int TJ>
-struct MirrorFull {   // full[mir] = sign * conj(full[full]) for the lane's elements
-    cplx<real>* full;
-    int lane;
-    template <int E>
-    __device__ __forceinline__ void apply() {
-        constexpr HM m = hm(E);
-        if constexpr (m.mir >= 0) {
-            if ((E & 31) == lane) {
-                const cplx<real> v = full[m.full];
-                const real sg = m.mirneg ? real(-1) : real(1);
-                full[m.mir] = {sg * v.re, -sg * v.im};
-            }
+__device__ __forceinline__ void mirror_full(cplx<real>* full, const ElemRT<real>* tab, int lane) {
+    for (int e = lane; e < Dims<TJ>::NHALF; e += 32) {
+        const ElemRT<real>& t = tab[e];
+        if (t.mir >= 0) {
+            const cplx<real> v = full[t.full];
+            const real sg = t.mirneg ? real(-1) : real(1);
+            full[t.mir] = {sg * v.re, -sg * v.im};
         }
     }
-};
+}
 
 template <typename real, int TJ>
-struct ExpandY {      // Y half (row-major) -> full layout with mirrors (lane's elements)
-    const cplx<real>* yh;
-    cplx<real>* full;
-    int lane;
-    template <int E>
-    __device__ __forceinline__ void apply() {
-        constexpr HM m = hm(E);
-        if ((E & 31) == lane) {
-            const cplx<real> v = yh[m.hidx];
-            full[m.full] = v;
-            if constexpr (m.mir >= 0) {
-                const real sg = m.mirneg ? real(-1) : real(1);
-                full[m.mir] = {sg * v.re, -sg * v.im};
-            }
+__device__ __forceinline__ void expand_y(const cplx<real>* yh, cplx<real>* full, const ElemRT<real>* tab, int lane) {
+    for (int e = lane; e < Dims<TJ>::NHALF; e += 32) {
+        const ElemRT<real>& t = tab[e];
+        const cplx<real> v = yh[t.hidx];
+        full[t.full] = v;
+        if (t.mir >= 0) {
+            const real sg = t.mirneg ? real(-1) : real(1);
+            full[t.mir] = {sg * v.re, -sg * v.im};
         }
     }
-};
+}
 
+// yw[0..3][E] = wD Y, wS Y, wP Y(q+1), wQ Y(q-1) in traversal order
 template <typename real, int TJ>
-struct WeightY {      // yw[0..3][E] = wD Y, wS Y, wP Y(q+1), wQ Y(q-1) (lane's elements)
-    const cplx<real>* full;
-    cplx<real>* yw;
-    int lane;
-    template <int E>
-    __device__ __forceinline__ void apply() {
-        constexpr HM m = hm(E);
-        constexpr int NH = Dims<TJ>::NHALF;
-        if ((E & 31) == lane) {
-            const cplx<real> y0 = full[m.full];
-            yw[E] = {real(m.wD) * y0.re, real(m.wD) * y0.im};
-            yw[NH + E] = {real(m.wS) * y0.re, real(m.wS) * y0.im};
-            const cplx<real> yp = full[m.yp >= 0 ? m.yp : m.full];
-            const cplx<real> ym = full[m.ym >= 0 ? m.ym : m.full];
-            yw[2 * NH + E] = {real(m.wP) * yp.re, real(m.wP) * yp.im};
-            yw[3 * NH + E] = {real(m.wQ) * ym.re, real(m.wQ) * ym.im};
-        }
+__device__ __forceinline__ void weight_y(const cplx<real>* full, cplx<real>* yw, const ElemRT<real>* tab, int lane) {
+    constexpr int NH = Dims<TJ>::NHALF;
+    for (int e = lane; e < NH; e += 32) {
+        const ElemRT<real>& t = tab[e];
+        const cplx<real> y0 = full[t.full];
+        yw[e] = {t.wD * y0.re, t.wD * y0.im};
+        yw[NH + e] = {t.wS * y0.re, t.wS * y0.im};
+        const cplx<real> yp = full[t.yp >= 0 ? t.yp : t.full];
+        const cplx<real> ym = full[t.ym >= 0 ? t.ym : t.full];
+        yw[2 * NH + e] = {t.wP * yp.re, t.wP * yp.im};
+        yw[3 * NH + e] = {t.wQ * ym.re, t.wQ * ym.im};
     }
-};
+}
 
 // ---- the per-atom pass -------------------------------------------------------------------------
 struct SnapV2Tables {
@@ -400,12 +412,12 @@ __device__ __forceinline__ void dedr_lane(const Vec4<real>& d, real kappa, real 
 // One round of 32 neighbours of the U pass (kept out of line so that the recursion's
 // element array is scalarised into registers).
 template <typename real, int TJ>
-__device__ __noinline__ void u_pass_round(WarpScratch2<real, TJ>& ws, int lane, int k, int cnt, real kappa, real rcut,
-                                          int sw, bool first) {
+__device__ __noinline__ void u_pass_round(WarpScratch2<real, TJ>& ws, const ElemRT<real>* tab, int lane, int k,
+                                          int cnt, real kappa, real rcut, int sw, bool first) {
     cplx<real> a{real(1), real(0)}, b{real(0), real(0)};
     real w = real(0);
     if (k < cnt) cayley_klein<real>(ws.disp[k], kappa, rcut, sw, a, b, w);
-    SinkU<real, TJ> sink{ws, lane, w, first};
+    SinkU<real, TJ> sink{ws, tab, lane, w, first};
     URec<real, TJ, SinkU<real, TJ>> rec(a, b, sink);
     ForE<0, Dims<TJ>::NHALF>::run(rec);
 }
@@ -431,7 +443,8 @@ __device__ __noinline__ void f_pass_round(WarpScratch2<real, TJ>& ws, int k, int
 }
 
 template <typename real, int TJ>
-__device__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const SnapV2Tables& yt, const real* __restrict__ cg,
+__device__ __noinline__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const ElemRT<real>* tab, const SnapV2Tables& yt,
+                                const real* __restrict__ cg,
                                 const real* __restrict__ beff, const SnapDevParams& sp, int lane, int n, int i,
                                 const double* q64, const float4* qf, const double box[3], int* nbr_out,
                                 int* nnb_out, real* dedr_out, cplx<real>* utot_out, int* status,
@@ -446,11 +459,8 @@ __device__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const SnapV2Tables& 
 
     // U_tot = I + sum_k w_k U(g_k): lane = neighbour, fixed-order sums over lanes
     for (int r = 0; r < (nround > 0 ? nround : 1); ++r)
-        u_pass_round<real, TJ>(ws, lane, r * 32 + lane, cnt, kappa, rcut, sp.switchflag, r == 0);
-    {
-        MirrorFull<real, TJ> mf{ws.full, lane};
-        ForE<0, NH>::run(mf);
-    }
+        u_pass_round<real, TJ>(ws, tab, lane, r * 32 + lane, cnt, kappa, rcut, sp.switchflag, r == 0);
+    mirror_full<real, TJ>(ws.full, tab, lane);
     __syncwarp();
     if (utot_out) {
         for (int e = lane; e < Dims<TJ>::NFULL; e += 32) utot_out[e] = ws.full[e];
@@ -465,15 +475,9 @@ __device__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const SnapV2Tables& 
     __syncwarp();
     y_rounds<real>(yt.jobs, yt.round_tb, yt.nrounds, lane, ws.full, cg, beff, ws.yh);
     __syncwarp();
-    {
-        ExpandY<real, TJ> ex{ws.yh, ws.full, lane};
-        ForE<0, NH>::run(ex);
-    }
+    expand_y<real, TJ>(ws.yh, ws.full, tab, lane);
     __syncwarp();
-    {
-        WeightY<real, TJ> wy{ws.full, ws.yw, lane};
-        ForE<0, NH>::run(wy);
-    }
+    weight_y<real, TJ>(ws.full, ws.yw, tab, lane);
     __syncwarp();
 
     // dE_i/dr_ik: lane = neighbour
