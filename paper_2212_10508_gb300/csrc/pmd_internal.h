@@ -63,7 +63,9 @@ struct SnapHostTables {
     double padded_terms = 0;          // term slots executed (lockstep padding included)
     // batched Y phase (FP32, lane = atom): int4 jobs (row, block) grouped by owning warp
     std::vector<int> sb_jobs;         // [njobs][4]
-    std::vector<int> sb_wptr;         // [twojmax + 1][SB_WARPS + 1] job ranges per stage tb and warp
+    std::vector<int> sb_rows;         // [nrows][2] job range of each (stage, row), stages concatenated
+    std::vector<int> sb_sptr;         // [nstages + 1] row ranges of the stages
+    std::vector<float> sb_coef;       // per-job Clebsch-Gordan weights (column, then row)
     double sb_load_max = 0, sb_load_avg = 0;
     // bispectrum jobs (energy path): per triple t the block id of (j1, j2, j)
     std::vector<int> tri_blk;
@@ -95,7 +97,9 @@ struct pmd_snap {
     pmd::DevBuf d_roundtb;   // uint8 [nrounds]
     pmd::DevBuf d_triblk;    // int4 per triple {blk, ta, tb, tj}
     pmd::DevBuf d_sbjobs;    // int4 jobs of the batched Y phase
-    pmd::DevBuf d_sbwptr;    // int [twojmax + 1][SB_WARPS + 1]
+    pmd::DevBuf d_sbrows;    // int2 job range per (stage, row)
+    pmd::DevBuf d_sbsptr;    // int [nstages + 1]
+    pmd::DevBuf d_sbcoef;    // float per-job Clebsch-Gordan weights
     // scratch
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_utot, s_B, s_status;
     int cap_atoms = 0;

@@ -121,72 +121,102 @@ __device__ __forceinline__ int active_members(const int* Ls, int nbatch, int ell
     return lo;
 }
 
-// Phase B for atom k of member m, one warp: force gather (lanes = neighbour slots), the
-// member's noise G_{ell,n} (lane 0 draws Philox block 0 -> G_x, G_y, lane 1 block 1 -> G_z) and
-// the Langevin update, lane al < 3 advancing component al.
+// Phase B of sub-step ell for the items it = first + r * stride, r < SB_B_GROUP, it < items, one
+// warp: the noise G_{ell,n} of all the group's atoms at once (lanes 2r and 2r+1 draw Philox
+// blocks 0 and 1 of atom r: G_x, G_y and G_z), the force gather of each atom (whole warp, lanes
+// = neighbour slots), and the Langevin update of all atoms at once (lane 3r + al advances
+// component al of atom r).  Positions and velocities are loaded before the gathers.
+constexpr int SB_B_GROUP = 8;
+
 template <typename real>
-__device__ __noinline__ void fine_phase_b(const FineArgs& a, int m, int k, int ell, int lane) {
+__device__ __noinline__ void fine_phase_b(const FineArgs& a, long first, long stride, long items, int ell, int lane) {
     const int n = a.n;
-    const int L = a.nsteps[m] < 0 ? 0 : a.nsteps[m];
-    double F[3];
-    warp_gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n,
-                            (const real*)a.dedr + (long)m * n * NMAX * 3, k, lane, F, a.status);
-    double* Q = a.q + m * a.stride;
-    double* V = a.vel + m * a.stride;
-    double* VH = a.vh + (long)m * 3 * n;
     const LangevinDev& Lp = a.L;
     const double box[3] = {a.box0, a.box1, a.box2};
-    const int64_t nid = a.ids[m];
-    const bool need_noise = Lp.scheme == PMD_SCHEME_PAPER || ell < L;
+    // this lane's roles: noise for atom rn = lane >> 1 (block lane & 1), update of atom ru = lane / 3
+    const int rn = lane >> 1, ru = lane / 3, al = lane - 3 * ru;
+    const long itn = first + (long)rn * stride, itu = first + (long)ru * stride;
     double g0 = 0.0, g1 = 0.0;
-    if (lane < 2 && need_noise) {
-        const uint64_t un = (uint64_t)nid;
-        uint32_t c[4] = {2u * (uint32_t)k + (uint32_t)lane, (uint32_t)ell, (uint32_t)un, (uint32_t)(un >> 32)};
-        philox4x32_10(c, (uint32_t)Lp.seed, (uint32_t)(Lp.seed >> 32));
-        box_muller(c, g0, g1);
+    if (rn < SB_B_GROUP && itn < items) {
+        const int m = a.order[itn / n], k = (int)(itn % n);
+        const int L = a.nsteps[m] < 0 ? 0 : a.nsteps[m];
+        if (Lp.scheme == PMD_SCHEME_PAPER || ell < L) {
+            const uint64_t un = (uint64_t)a.ids[m];
+            uint32_t c[4] = {2u * (uint32_t)k + (uint32_t)(lane & 1), (uint32_t)ell, (uint32_t)un, (uint32_t)(un >> 32)};
+            philox4x32_10(c, (uint32_t)Lp.seed, (uint32_t)(Lp.seed >> 32));
+            box_muller(c, g0, g1);
+        }
     }
-    const double gx = __shfl_sync(0xffffffffu, g0, 0), gy = __shfl_sync(0xffffffffu, g1, 0);
-    const double gz = __shfl_sync(0xffffffffu, g0, 1);
-    if (lane < 3) {
-        const int al = lane;
-        const double Fa = al == 0 ? F[0] : (al == 1 ? F[1] : F[2]);
-        const double G = al == 0 ? gx : (al == 1 ? gy : gz);
-        const long e = (long)al * n + k;
+    // update lanes: state of component al of atom ru
+    const bool upd = ru < SB_B_GROUP && itu < items;
+    int mu = 0, ku = 0, Lu = 0;
+    double qv = 0.0, vv = 0.0, vhv = 0.0;
+    long e = 0;
+    if (upd) {
+        mu = a.order[itu / n];
+        ku = (int)(itu % n);
+        Lu = a.nsteps[mu] < 0 ? 0 : a.nsteps[mu];
+        e = (long)al * n + ku;
+        qv = a.q[mu * a.stride + e];
+        vv = a.vel[mu * a.stride + e];
+        vhv = a.vh[(long)mu * 3 * n + e];
+    }
+    // gathers, one atom at a time; lane 3r + al keeps component al of atom r
+    double Fa = 0.0;
+    for (int r = 0; r < SB_B_GROUP; ++r) {
+        const long it = first + (long)r * stride;
+        if (it >= items) break;
+        const int m = a.order[it / n], k = (int)(it % n);
+        double F[3];
+        warp_gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n,
+                                (const real*)a.dedr + (long)m * n * NMAX * 3, k, lane, F, a.status);
+        if (ru == r) Fa = al == 0 ? F[0] : (al == 1 ? F[1] : F[2]);
+    }
+    // G of (ru, al): G_x, G_y from lane 2 ru, G_z from lane 2 ru + 1
+    const int src = 2 * (ru < SB_B_GROUP ? ru : 0) + (al == 2 ? 1 : 0);
+    const double s0 = __shfl_sync(0xffffffffu, g0, src), s1 = __shfl_sync(0xffffffffu, g1, src);
+    const double G = al == 1 ? s1 : s0;
+    double qn = qv;
+    if (upd) {
         bool bad = false;
+        double* Q = a.q + mu * a.stride;
+        double* V = a.vel + mu * a.stride;
+        double* VH = a.vh + (long)mu * 3 * n;
         if (Lp.scheme == PMD_SCHEME_PAPER) {
             const double s = sched_sigma(Lp, ell);
-            double v = V[e];
-            double vh = ell == 0 ? v : VH[e];
+            double v = vv;
+            const double vh = ell == 0 ? v : vhv;
             if (ell > 0) v = half_kick(Lp, vh, Fa, vh, s, G);           // finish step ell-1
-            if (ell < L) {
-                double vhn = half_kick(Lp, v, Fa, vh, s, G);            // first half of step ell
-                double qn = drift(Q[e], Lp.dt, vhn);
+            if (ell < Lu) {
+                const double vhn = half_kick(Lp, v, Fa, vh, s, G);      // first half of step ell
+                qn = drift(qv, Lp.dt, vhn);
                 if (!isfinite(qn)) bad = true;
-                if (fabs(qn - Q[e]) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
+                if (fabs(qn - qv) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
                 Q[e] = qn;
                 VH[e] = vhn;
             }
             V[e] = v;
         } else {
-            double v = V[e];
+            double v = vv;
             if (ell > 0) v = kick_b(Lp, v, Fa);
-            if (ell < L) {
-                double q = Q[e];
-                const double q0 = q;
+            if (ell < Lu) {
+                double q = qv;
                 v = kick_b(Lp, v, Fa);
                 q = __dadd_rn(q, __dmul_rn(Lp.hdt, v));
                 v = ou_o(Lp, v, G);
                 q = __dadd_rn(q, __dmul_rn(Lp.hdt, v));
                 if (!isfinite(q)) bad = true;
-                if (fabs(q - q0) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
+                if (fabs(q - qv) > 0.5 * box[al]) flag(a.status, ST_LOSTATOM);
                 Q[e] = q;
+                qn = q;
             }
             V[e] = v;
         }
         if (bad) flag(a.status, ST_NONFINITE);
     }
-    __syncwarp();
-    if (lane == 0 && ell < L && sizeof(real) == 4) a.qf[(long)m * n + k] = wrap_f32(Q[k], Q[n + k], Q[2 * n + k], box);
+    // wrapped FP32 copy of the new position (lane 3r assembles the three components)
+    const double qy = __shfl_down_sync(0xffffffffu, qn, 1), qz = __shfl_down_sync(0xffffffffu, qn, 2);
+    if (sizeof(real) == 4 && upd && al == 0 && ell < Lu) a.qf[(long)mu * n + ku] = wrap_f32(qn, qy, qz, box);
 }
 
 // Phase A of sub-step ell over the items (active member, atom) = [0, A n).
@@ -208,7 +238,7 @@ __device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, lo
                 return SBAtom{a.q + m * a.stride, a.qf + m * n, i, a.nbr + ai * NMAX, a.nnb + ai,
                               (float*)a.dedr + ai * NMAX * 3, nullptr};
             };
-            sb_batch<TJ>(sh, a.v.sbjobs, a.v.sbwptr, a.v.sp, na, at, n, box, a.status, true);
+            sb_batch<TJ>(sh, a.v.sbjobs, a.v.sbrows, a.v.sbsptr, a.v.sbcoef, a.v.sp, na, at, n, box, a.status, true);
         }
     } else {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -239,11 +269,8 @@ __device__ __forceinline__ void fine_loop(const FineArgs& a, const SH& sh) {
         const long items = (long)A * n;
         fine_phase_a<real, TJ>(a, sh, items, box);
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
-        for (long it = gwarp; it < items; it += nwarps) {
-            const int m = a.order[it / n];
-            const int k = (int)(it % n);
-            fine_phase_b<real>(a, m, k, ell, lane);
-        }
+        for (long first = gwarp; first < items; first += (long)SB_B_GROUP * nwarps)
+            fine_phase_b<real>(a, first, nwarps, items, ell, lane);
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
     }
 }

@@ -33,21 +33,41 @@ static double clebsch(int tj1, int tm1, int tj2, int tm2, int tJ, int tM) {
 
 // Jobs of the batched Y phase (lane = atom).  A job is one output row (tj, p) of the half
 // layout of Y and one block (ta, tb, J = tj); it covers the row's h_ncol(tj) outputs.  The Y
-// phase runs in twojmax + 1 stages, one per sub-block size tb, separated by CTA barriers (so
-// that the CTA executes the unrolled code of one tb at a time).  Within a stage whole rows are
-// assigned to the SB_WARPS warps (longest-processing-time first on a cost model of the FP and
-// load instructions): each output is updated by one warp per stage, in a fixed order, and the
-// stages are ordered by the barriers, so the sums are deterministic.  Each warp's jobs of a stage
-// are ordered by row width.
+// phase runs in stages of sub-block sizes (tb <= SB_SMALL_TB together, then one stage per larger
+// tb) separated by CTA barriers, so that the CTA executes the unrolled code of few variants at a
+// time.  A stage is a list of rows, longest first (cost model of the FP and load instructions);
+// warps take rows from a shared counter, and a row's jobs of the stage run in a fixed order on the
+// warp that took it.  Each output's update sequence is therefore fixed (stages in order, then the
+// row's jobs in order) whatever warp runs it: the sums are deterministic.
+// Coefficient record of one job (float offset, a multiple of 4, into T->sb_coef): first the
+// column weights c2[o][k] = <a q1, b tb-k | J q> with q = qlo + o, q1 = q + s - tb + k (zero where
+// q1 is outside 0..ta), o < h_ncol(J), k <= tb; then the row weights c1[i] = <a p1, b tb-i | J p>
+// with p1 = p + s - tb + i (zero outside 0..ta); padded to a multiple of 4.
+static int append_job_coefs(SnapHostTables* T, int blk, int tj, int p) {
+    const int ta = T->blk_ta[blk], tb = T->blk_tb[blk], nc = ncol_half(tj);
+    const double* cg = T->cg.data() + T->blk_cgoff[blk];
+    const int s = (ta + tb - tj) / 2, p10 = p + s - tb, c0 = qlo(tj) + s - tb;
+    const int off = (int)T->sb_coef.size();
+    for (int o = 0; o < nc; ++o)
+        for (int k = 0; k <= tb; ++k) {
+            const int q1 = c0 + o + k;
+            T->sb_coef.push_back(q1 >= 0 && q1 <= ta ? (float)cg[q1 * (tb + 1) + (tb - k)] : 0.f);
+        }
+    for (int i = 0; i <= tb; ++i) {
+        const int p1 = p10 + i;
+        T->sb_coef.push_back(p1 >= 0 && p1 <= ta ? (float)cg[p1 * (tb + 1) + (tb - i)] : 0.f);
+    }
+    while (T->sb_coef.size() % 4) T->sb_coef.push_back(0.f);
+    return off;
+}
+
 static void build_batch_jobs(SnapHostTables* T) {
     struct RJ {
         int tj, p, blk, ta, tb;
-        double cost;
     };
-    const int NTB = T->twojmax + 1;
     const int nblk = (int)T->blk_ta.size();
-    // per stage tb: rows (tj, p) -> their jobs
-    std::vector<std::map<std::pair<int, int>, std::vector<RJ>>> stage(NTB);
+    const int nstage = sb_num_stages(T->twojmax);
+    std::vector<std::map<std::pair<int, int>, std::pair<double, std::vector<RJ>>>> stage(nstage);
     for (int tj = 0; tj <= T->twojmax; ++tj) {
         const int nc = ncol_half(tj);
         for (int p = 0; p <= tj; ++p)
@@ -64,42 +84,39 @@ static void build_batch_jobs(SnapHostTables* T) {
                     ++loads;
                     for (int o = 0; o < nc; ++o) terms += (w - o >= 0 && w - o <= tb);
                 }
-                const double cost = ni * (6.0 * terms + 2.0 * loads) + nc * (tb + 1) + 4.0 * nc;
-                stage[tb][{tj, p}].push_back({tj, p, id, ta, tb, cost});
+                auto& row = stage[sb_stage_of(tb)][{tj, p}];
+                row.first += ni * (6.0 * terms + 2.0 * loads) + nc * (tb + 1) + 4.0 * nc + 20.0;
+                row.second.push_back({tj, p, id, ta, tb});
             }
     }
     T->sb_jobs.clear();
-    T->sb_wptr.assign((size_t)NTB * (SB_WARPS + 1), 0);
+    T->sb_rows.clear();
+    T->sb_coef.clear();
+    T->sb_sptr.assign(nstage + 1, 0);
     T->sb_load_max = 0.0;
     T->sb_load_avg = 0.0;
-    for (int tb = 0; tb < NTB; ++tb) {
+    for (int st = 0; st < nstage; ++st) {
         std::vector<std::pair<double, std::pair<int, int>>> rows;
-        for (auto& kv : stage[tb]) {
-            double c = 0.0;
-            for (const RJ& j : kv.second) c += j.cost;
-            rows.push_back({c, kv.first});
-        }
+        for (auto& kv : stage[st]) rows.push_back({kv.second.first, kv.first});
         std::stable_sort(rows.begin(), rows.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        // expected makespan of the greedy take-next order (for the record)
         std::vector<double> load(SB_WARPS, 0.0);
-        std::vector<std::vector<RJ>> wj(SB_WARPS);
         for (auto& r : rows) {
-            const int w = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            load[w] += r.first;
-            for (const RJ& j : stage[tb][r.second]) wj[w].push_back(j);
-        }
-        int* wp = &T->sb_wptr[(size_t)tb * (SB_WARPS + 1)];
-        wp[0] = (int)T->sb_jobs.size() / 4;
-        for (int w = 0; w < SB_WARPS; ++w) {
-            std::stable_sort(wj[w].begin(), wj[w].end(),
-                             [](const RJ& x, const RJ& y) { return ncol_half(x.tj) < ncol_half(y.tj); });
-            for (const RJ& j : wj[w]) {
+            auto it = std::min_element(load.begin(), load.end());
+            *it += r.first;
+            std::vector<RJ> js = stage[st][r.second].second;
+            std::stable_sort(js.begin(), js.end(), [](const RJ& x, const RJ& y) { return x.tb < y.tb; });
+            const int j0 = (int)T->sb_jobs.size() / 4;
+            for (const RJ& j : js) {
                 T->sb_jobs.push_back(j.ta | (j.tb << 4) | (j.tj << 8) | (j.p << 12));
-                T->sb_jobs.push_back(T->blk_cgoff[j.blk]);
+                T->sb_jobs.push_back(append_job_coefs(T, j.blk, j.tj, j.p));
                 T->sb_jobs.push_back(uoff_full(j.ta) | (uoff_full(j.tb) << 16));
                 T->sb_jobs.push_back((T->hoff[j.tj] + j.p * ncol_half(j.tj)) | (j.blk << 16));
             }
-            wp[w + 1] = (int)T->sb_jobs.size() / 4;
+            T->sb_rows.push_back(j0);
+            T->sb_rows.push_back((int)T->sb_jobs.size() / 4);
         }
+        T->sb_sptr[st + 1] = (int)T->sb_rows.size() / 2;
         double tot = 0.0;
         for (double x : load) tot += x;
         T->sb_load_max += *std::max_element(load.begin(), load.end());
@@ -301,8 +318,12 @@ static int upload_tables(pmd_snap* s) {
     PMD_CUDA_TRY(cudaMemcpy(s->d_roundtb.p, T.round_tb.data(), T.round_tb.size(), cudaMemcpyHostToDevice));
     if ((rc = s->d_sbjobs.ensure(std::max<size_t>(1, T.sb_jobs.size()) * sizeof(int)))) return rc;
     PMD_CUDA_TRY(cudaMemcpy(s->d_sbjobs.p, T.sb_jobs.data(), T.sb_jobs.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if ((rc = s->d_sbwptr.ensure(T.sb_wptr.size() * sizeof(int)))) return rc;
-    PMD_CUDA_TRY(cudaMemcpy(s->d_sbwptr.p, T.sb_wptr.data(), T.sb_wptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbcoef.ensure(std::max<size_t>(4, T.sb_coef.size()) * sizeof(float)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbcoef.p, T.sb_coef.data(), T.sb_coef.size() * sizeof(float), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbrows.ensure(std::max<size_t>(1, T.sb_rows.size()) * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbrows.p, T.sb_rows.data(), T.sb_rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbsptr.ensure(T.sb_sptr.size() * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbsptr.p, T.sb_sptr.data(), T.sb_sptr.size() * sizeof(int), cudaMemcpyHostToDevice));
     std::vector<int4> tb(T.nB);
     for (int t = 0; t < T.nB; ++t) {
         const int b = T.tri_blk[t];
@@ -327,7 +348,9 @@ SnapView snap_view(const pmd_snap* s, const double* beta) {
     v.yt.round_tb = s->d_roundtb.as<unsigned char>();
     v.yt.nrounds = s->T.nrounds;
     v.sbjobs = s->d_sbjobs.as<int4>();
-    v.sbwptr = s->d_sbwptr.as<int>();
+    v.sbrows = s->d_sbrows.as<int2>();
+    v.sbcoef = s->d_sbcoef.as<float>();
+    v.sbsptr = s->d_sbsptr.as<int>();
     v.beta = beta;
     v.ncg = (int)s->T.cg.size();
     v.nblk = (int)s->T.blk_ta.size();
@@ -378,7 +401,7 @@ __global__ void __launch_bounds__(snap_cta_threads<real>(), 1)
                 return SBAtom{pos + bb * 3 * n, qf + bb * n, (int)(item % n), nbr + item * NMAX, nnb + item,
                               dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr};
             };
-            sb_batch<TJ>(sh, v.sbjobs, v.sbwptr, v.sp, na, at, n, box, status, want_forces != 0);
+            sb_batch<TJ>(sh, v.sbjobs, v.sbrows, v.sbsptr, v.sbcoef, v.sp, na, at, n, box, status, want_forces != 0);
         }
     } else {
         SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, v);

@@ -5,10 +5,10 @@
 //            of U(a_k, b_k) (snap_v2.cuh) and the lanes' weighted values are summed over the 32
 //            lanes in a fixed order.  U_tot of the batch is kept in shared memory as
 //            [element][atom] with a padded leading dimension (SB_LD = 33).
-//  Y phase : lane = atom.  Y^J = sum_blocks beta_eff(J,a,b) Z^J_{ab} on the half layout, in one
-//            stage per sub-block size b (CTA barrier in between: one size's unrolled code at a
-//            time).  In a stage every warp owns whole output rows (J, m') and runs, per block, the
-//            Clebsch-Gordan double sum of the row's outputs: for each row m1' of U^a, the window of U^a columns that
+//  Y phase : lane = atom.  Y^J = sum_blocks beta_eff(J,a,b) Z^J_{ab} on the half layout, in
+//            stages of sub-block sizes b (CTA barrier in between: few variants of unrolled code
+//            at a time).  In a stage warps take whole output rows (J, m') from a shared counter
+//            and run, per block, the Clebsch-Gordan double sum of the row's outputs: for each row m1' of U^a, the window of U^a columns that
 //            the row's outputs share and one row of U^b are loaded once into registers and
 //            reused by all outputs.  Loop bounds skip out-of-range terms, all control flow and
 //            index arithmetic is warp-uniform, and every lane reads its own atom's element
@@ -27,28 +27,40 @@ constexpr int SB_LD = 33;                 // leading dimension of the [element][
 constexpr int SB_WARPS = 16;
 constexpr int SB_THREADS = SB_WARPS * 32;
 constexpr int SB_CHUNK = 8;               // U-pass elements summed per lane-sum round
+constexpr int SB_SMALL_TB = 3;            // sub-block sizes tb <= this share one Y stage
+constexpr int SB_MAX_STAGES = 16;
+constexpr int SB_GUARD = 16;              // zero rows before and after U_tot (>= twojmax)
+
+// Y stages: tb <= SB_SMALL_TB together, then one per larger tb
+__host__ __device__ constexpr int sb_stage_of(int tb) { return tb <= SB_SMALL_TB ? 0 : tb - SB_SMALL_TB; }
+__host__ __device__ constexpr int sb_num_stages(int twojmax) { return sb_stage_of(twojmax) + 1; }
 
 // Shared memory of one CTA.  Aliases: the U-pass lane buffers live in the Y array (unused
 // during the U phase), the weighted Y copies of the dE/dr phase in the U array (unused after
 // the Y phase).
 template <int TJ>
 struct SBShared {
-    float* cg;                 // Clebsch-Gordan blocks
     float* beff;               // beta_eff per block
     ElemRT<float>* tab;        // element table (traversal order)
     float2* ut;                // [NFULL][SB_LD] U_tot of the batch
     float2* yt;                // [NHALF][SB_LD] Y of the batch (row-major half index)
     int* nbr;                  // [SB_ATOMS][NMAX]
     int* nnb;                  // [SB_ATOMS]
+    int* ctr;                  // [SB_MAX_STAGES] row counters of the Y stages
     Vec4<float>* disp;         // [SB_ATOMS][NMAX]
     __device__ float2* lv(int warp) const { return yt + warp * SB_CHUNK * SB_LD; }
     __device__ float2* yw(int warp) const { return ut + warp * 3 * Dims<TJ>::NHALF; }
 };
 
+// U_tot region: SB_GUARD zero rows, NFULL rows, SB_GUARD zero rows.  The Y phase reads whole
+// column windows of U^a rows; slots outside the row (zero weight) read a neighbouring row or a
+// guard row, never outside the region.  The weighted Y copies of the dE/dr phase alias the NFULL
+// rows only, so the guards stay zero.
 template <int TJ>
 __host__ __device__ constexpr size_t sb_ut_elems() {
-    const size_t a = (size_t)Dims<TJ>::NFULL * SB_LD, b = (size_t)SB_WARPS * 3 * Dims<TJ>::NHALF;
-    return a > b ? a : b;
+    static_assert((size_t)SB_WARPS * 3 * Dims<TJ>::NHALF <= (size_t)Dims<TJ>::NFULL * SB_LD, "yw alias");
+    static_assert(SB_GUARD >= TJ, "guard rows");
+    return (size_t)(Dims<TJ>::NFULL + 2 * SB_GUARD) * SB_LD;
 }
 template <int TJ>
 __host__ __device__ constexpr size_t sb_yt_elems() {
@@ -115,56 +127,60 @@ __device__ __noinline__ void sb_u_round(float2* lv, float2* ut, const Vec4<float
 // and one block (ta, tb = TB, J = tj), s = (ta + tb - tj)/2.  Output (p, q) sums over rows
 // p1 = p + s - TB + i of U^a (i = 0..TB, p2 = TB - i) and columns q1 = q + s - TB + k of U^a
 // (k = 0..TB, q2 = TB - k):  C(p1, p2) C(q1, q2) U^a[p1][q1] U^b[p2][q2].  With the window
-// slot w = q1 - (qlo + s - TB), output o = q - qlo uses slot w = o + k.
-// Job record: x = ta | tb << 4 | tj << 8 | p << 12; y = CG offset of the block;
+// slot w = q1 - (qlo + s - TB), output o = q - qlo uses slot w = o + k.  All TB + NC slots are
+// read (no per-slot test): out-of-range columns carry zero weight.
+// Job record: x = ta | tb << 4 | tj << 8 | p << 12; y = offset of the job's weights in coef
+// (column weights c2[o][k], zero where q1 is out of range, then row weights c1[i]);
 // z = full offset of U^a | full offset of U^b << 16; w = half index of (tj, p, qlo) | blk << 16.
 template <int TB, int NC>
-__device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__ ut, const float* __restrict__ cg,
+__device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__ ut, const float* __restrict__ coef,
                                         const float* __restrict__ beff, float2* __restrict__ yt, int lane) {
     const int ta = J.x & 15, tj = (J.x >> 8) & 15, p = (J.x >> 12) & 15;
     const int s = (ta + TB - tj) >> 1;
     const int p10 = p + s - TB;
     const int c0 = ((tj + 1) >> 1) + s - TB;
-    const float* c = cg + J.y;
-    float c2[NC][TB + 1];
+    constexpr int N2 = NC * (TB + 1), NV = (N2 + 3) / 4;
+    float c2[NV * 4];
+    const float4* cp = reinterpret_cast<const float4*>(coef + J.y);
 #pragma unroll
-    for (int o = 0; o < NC; ++o)
-#pragma unroll
-        for (int k = 0; k <= TB; ++k) {
-            const int q1 = c0 + o + k;
-            const bool ok = q1 >= 0 && q1 <= ta;
-            c2[o][k] = ok ? c[(ok ? q1 : 0) * (TB + 1) + (TB - k)] : 0.f;
-        }
+    for (int v = 0; v < NV; ++v) {
+        const float4 t = __ldg(cp + v);
+        c2[4 * v] = t.x;
+        c2[4 * v + 1] = t.y;
+        c2[4 * v + 2] = t.z;
+        c2[4 * v + 3] = t.w;
+    }
+    const float* c1p = coef + J.y + N2;
     const int ilo = p10 < 0 ? -p10 : 0;
     const int ihi = ta - p10 < TB ? ta - p10 : TB;
-    const int wlo = c0 < 0 ? -c0 : 0, whi = ta - c0;
     const int ua = J.z & 0xffff, ub = J.z >> 16;
     float zr[NC], zi[NC];
 #pragma unroll
     for (int o = 0; o < NC; ++o) zr[o] = zi[o] = 0.f;
     for (int i = ilo; i <= ihi; ++i) {
         const int p1 = p10 + i;
-        const float c1 = c[p1 * (TB + 1) + (TB - i)];
+        const float c1 = __ldg(c1p + i);
         const float2* yb = ut + (ub + (TB - i) * (TB + 1)) * SB_LD + lane;
         float2 y[TB + 1];
 #pragma unroll
         for (int k = 0; k <= TB; ++k) y[k] = yb[(TB - k) * SB_LD];
-        const int xrow = ua + p1 * (ta + 1) + c0;   // window slot 0 (only valid slots are read)
+        // window slot 0; slots whose column falls outside 0..ta have zero weight
+        const float2* xb = ut + (ua + p1 * (ta + 1) + c0) * SB_LD + lane;
         float tr[NC], ti[NC];
 #pragma unroll
         for (int o = 0; o < NC; ++o) tr[o] = ti[o] = 0.f;
 #pragma unroll
         for (int w = 0; w < TB + NC; ++w) {
-            if (w < wlo || w > whi) continue;
-            const float2 x = ut[(xrow + w) * SB_LD + lane];
+            const float2 x = xb[w * SB_LD];
 #pragma unroll
             for (int o = 0; o < NC; ++o) {
                 const int k = w - o;
                 if (k < 0 || k > TB) continue;
+                const float cc = c2[o * (TB + 1) + k];
                 const float pr = x.x * y[k].x - x.y * y[k].y;
                 const float pi = x.x * y[k].y + x.y * y[k].x;
-                tr[o] += c2[o][k] * pr;
-                ti[o] += c2[o][k] * pi;
+                tr[o] += cc * pr;
+                ti[o] += cc * pi;
             }
         }
 #pragma unroll
@@ -182,9 +198,10 @@ __device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__
     }
 }
 
+// Jobs [j0, j1) of one row, in order.
 template <int TJ>
-__device__ __noinline__ void sb_y_phase(const int4* __restrict__ jobs, int j0, int j1, const float2* ut,
-                                        const float* cg, const float* beff, float2* yt, int lane) {
+__device__ __noinline__ void sb_y_row(const int4* __restrict__ jobs, int j0, int j1, const float2* ut,
+                                      const float* coef, const float* beff, float2* yt, int lane) {
     for (int j = j0; j < j1; ++j) {
         const int4 J = jobs[j];
         const int tb = (J.x >> 4) & 15, tj = (J.x >> 8) & 15;
@@ -192,7 +209,7 @@ __device__ __noinline__ void sb_y_phase(const int4* __restrict__ jobs, int j0, i
         switch (nc * 16 + tb) {
 #define PMD_SB_CASE(NC_, TB_)                                                         \
     case NC_ * 16 + TB_:                                                              \
-        if constexpr (TB_ <= TJ && NC_ <= h_ncol(TJ)) sb_yjob<TB_, NC_>(J, ut, cg, beff, yt, lane); \
+        if constexpr (TB_ <= TJ && NC_ <= h_ncol(TJ)) sb_yjob<TB_, NC_>(J, ut, coef, beff, yt, lane); \
         break;
 #define PMD_SB_ROW(NC_)                                                                          \
     PMD_SB_CASE(NC_, 0) PMD_SB_CASE(NC_, 1) PMD_SB_CASE(NC_, 2) PMD_SB_CASE(NC_, 3)              \
@@ -206,6 +223,29 @@ __device__ __noinline__ void sb_y_phase(const int4* __restrict__ jobs, int j0, i
 #undef PMD_SB_CASE
             default: break;
         }
+    }
+}
+
+// The whole Y phase of a batch (all threads of the CTA; ends with a CTA barrier).
+template <int TJ>
+__device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const int4* __restrict__ jobs,
+                                           const int2* __restrict__ rows, const int* __restrict__ sptr,
+                                           const float* __restrict__ coef, int lane) {
+    for (int x = threadIdx.x; x < Dims<TJ>::NHALF * SB_LD; x += blockDim.x) sh.yt[x] = make_float2(0.f, 0.f);
+    if (threadIdx.x < SB_MAX_STAGES) sh.ctr[threadIdx.x] = 0;
+    __syncthreads();
+    for (int st = 0; st < sb_num_stages(TJ); ++st) {   // stages of sub-block sizes
+        const int r0 = sptr[st], r1 = sptr[st + 1];
+        if (r0 == r1) continue;
+        for (;;) {
+            int r = 0;
+            if (lane == 0) r = atomicAdd(&sh.ctr[st], 1);
+            r = r0 + __shfl_sync(0xffffffffu, r, 0);
+            if (r >= r1) break;
+            const int2 R = rows[r];
+            sb_y_row<TJ>(jobs, R.x, R.y, sh.ut, coef, sh.beff, sh.yt, lane);
+        }
+        __syncthreads();
     }
 }
 
@@ -291,7 +331,8 @@ struct SBAtom {
 // All threads of the CTA call it with the same arguments.  at(slot) returns the SBAtom of the
 // batch's atom slot (slot < na).  Ends with a CTA barrier.
 template <int TJ, class AtomOf>
-__device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, const int* __restrict__ wptr,
+__device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, const int2* __restrict__ rows,
+                         const int* __restrict__ sptr, const float* __restrict__ coef,
                          const SnapDevParams& sp, int na, const AtomOf& at, int n, const double box[3], int* status,
                          bool want_forces) {
     constexpr int NH = Dims<TJ>::NHALF, NF = Dims<TJ>::NFULL;
@@ -337,15 +378,7 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, 
     __syncthreads();
     if (!want_forces) return;
 
-    // Y phase
-    for (int x = threadIdx.x; x < NH * SB_LD; x += blockDim.x) sh.yt[x] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int tb = 0; tb <= TJ; ++tb) {   // one stage per sub-block size
-        const int* wp = wptr + tb * (SB_WARPS + 1);
-        if (wp[0] == wp[SB_WARPS]) continue;
-        sb_y_phase<TJ>(jobs, wp[warp], wp[warp + 1], sh.ut, sh.cg, sh.beff, sh.yt, lane);
-        __syncthreads();
-    }
+    sb_y_phase<TJ>(sh, jobs, rows, sptr, coef, lane);
 
     // dE/dr phase
     for (int slot = warp; slot < na; slot += SB_WARPS) {

@@ -17,7 +17,9 @@ struct SnapView {
     const double* beffc;
     SnapV2Tables yt;
     const int4* sbjobs;      // batched Y phase jobs (FP32 design)
-    const int* sbwptr;       // [twojmax + 1][SB_WARPS + 1] job ranges per stage and warp
+    const int2* sbrows;      // job range of each (stage, row)
+    const int* sbsptr;       // row ranges of the stages
+    const float* sbcoef;     // per-job Clebsch-Gordan weights
     const double* beta;
     int ncg, nblk, nB;
     SnapDevParams sp;
@@ -79,13 +81,13 @@ __device__ inline void snap_shared_load(SnapShared<real, TJ>& sh, const SnapView
 template <int TJ>
 __host__ __device__ inline size_t sb_shared_bytes(const SnapView& v) {
     size_t o = 0;
-    o = align_up(o + (size_t)v.ncg * sizeof(float), 32);
     o = align_up(o + (size_t)v.nblk * sizeof(float), 32);
     o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<float>), 32);
     o = align_up(o + sb_ut_elems<TJ>() * sizeof(float2), 32);
     o = align_up(o + sb_yt_elems<TJ>() * sizeof(float2), 32);
     o = align_up(o + (size_t)SB_ATOMS * NMAX * sizeof(int), 32);
     o = align_up(o + (size_t)SB_ATOMS * sizeof(int), 32);
+    o = align_up(o + (size_t)SB_MAX_STAGES * sizeof(int), 32);
     o = align_up(o + (size_t)SB_ATOMS * NMAX * sizeof(Vec4<float>), 32);
     return o;
 }
@@ -94,13 +96,11 @@ template <int TJ>
 __device__ inline SBShared<TJ> sb_shared_carve(unsigned char* smem, const SnapView& v) {
     SBShared<TJ> sh;
     size_t o = 0;
-    sh.cg = reinterpret_cast<float*>(smem + o);
-    o = align_up(o + (size_t)v.ncg * sizeof(float), 32);
     sh.beff = reinterpret_cast<float*>(smem + o);
     o = align_up(o + (size_t)v.nblk * sizeof(float), 32);
     sh.tab = reinterpret_cast<ElemRT<float>*>(smem + o);
     o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<float>), 32);
-    sh.ut = reinterpret_cast<float2*>(smem + o);
+    sh.ut = reinterpret_cast<float2*>(smem + o) + SB_GUARD * SB_LD;
     o = align_up(o + sb_ut_elems<TJ>() * sizeof(float2), 32);
     sh.yt = reinterpret_cast<float2*>(smem + o);
     o = align_up(o + sb_yt_elems<TJ>() * sizeof(float2), 32);
@@ -108,20 +108,24 @@ __device__ inline SBShared<TJ> sb_shared_carve(unsigned char* smem, const SnapVi
     o = align_up(o + (size_t)SB_ATOMS * NMAX * sizeof(int), 32);
     sh.nnb = reinterpret_cast<int*>(smem + o);
     o = align_up(o + (size_t)SB_ATOMS * sizeof(int), 32);
+    sh.ctr = reinterpret_cast<int*>(smem + o);
+    o = align_up(o + (size_t)SB_MAX_STAGES * sizeof(int), 32);
     sh.disp = reinterpret_cast<Vec4<float>*>(smem + o);
     return sh;
 }
 
 template <int TJ>
 __device__ inline void sb_shared_load(SBShared<TJ>& sh, const SnapView& v) {
-    const float* cg = reinterpret_cast<const float*>(v.cg);
-    for (int x = threadIdx.x; x < v.ncg; x += blockDim.x) sh.cg[x] = cg[x];
     for (int b = threadIdx.x; b < v.nblk; b += blockDim.x) {
         double s = 0.0;
         for (int c = v.beffptr[b]; c < v.beffptr[b + 1]; ++c) s += v.beffc[c] * v.beta[1 + v.befft[c]];
         sh.beff[b] = (float)s;
     }
     fill_elem_table<float, TJ>(sh.tab);
+    for (int x = threadIdx.x; x < SB_GUARD * SB_LD; x += blockDim.x) {
+        sh.ut[x - SB_GUARD * SB_LD] = make_float2(0.f, 0.f);
+        sh.ut[(size_t)Dims<TJ>::NFULL * SB_LD + x] = make_float2(0.f, 0.f);
+    }
 }
 
 // threads per CTA of the SNAP kernels: the batched FP32 design or one warp per atom (FP64)
