@@ -128,7 +128,10 @@ __device__ __noinline__ void sb_u_round(float2* lv, float2* ut, const Vec4<float
 // p1 = p + s - TB + i of U^a (i = 0..TB, p2 = TB - i) and columns q1 = q + s - TB + k of U^a
 // (k = 0..TB, q2 = TB - k):  C(p1, p2) C(q1, q2) U^a[p1][q1] U^b[p2][q2].  With the window
 // slot w = q1 - (qlo + s - TB), output o = q - qlo uses slot w = o + k.  All TB + NC slots are
-// read (no per-slot test): out-of-range columns carry zero weight.
+// read (no per-slot test): out-of-range columns carry zero weight.  Arithmetic on FP32 pairs
+// (sm_100+ paired FMA): per term cx = c2 (xr, xi), S += cx * (yr, yi), T += cx * (yi, yr), so
+// that S = (sum c xr yr, sum c xi yi) and T = (sum c xr yi, sum c xi yr); each row's S and T are
+// scaled by its weight c1 and Z = (S.x - S.y, T.x + T.y) is formed once per job.
 // Job record: x = ta | tb << 4 | tj << 8 | p << 12; y = offset of the job's weights in coef
 // (column weights c2[o][k], zero where q1 is out of range, then row weights c1[i]);
 // z = full offset of U^a | full offset of U^b << 16; w = half index of (tj, p, qlo) | blk << 16.
@@ -154,21 +157,24 @@ __device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__
     const int ilo = p10 < 0 ? -p10 : 0;
     const int ihi = ta - p10 < TB ? ta - p10 : TB;
     const int ua = J.z & 0xffff, ub = J.z >> 16;
-    float zr[NC], zi[NC];
+    // paired accumulators: zS = sum c1 c2 (xr yr, xi yi), zT = sum c1 c2 (xr yi, xi yr)
+    float2 zS[NC], zT[NC];
 #pragma unroll
-    for (int o = 0; o < NC; ++o) zr[o] = zi[o] = 0.f;
+    for (int o = 0; o < NC; ++o) zS[o] = zT[o] = make_float2(0.f, 0.f);
     for (int i = ilo; i <= ihi; ++i) {
         const int p1 = p10 + i;
         const float c1 = __ldg(c1p + i);
         const float2* yb = ut + (ub + (TB - i) * (TB + 1)) * SB_LD + lane;
-        float2 y[TB + 1];
+        float2 y[TB + 1], ys[TB + 1];
 #pragma unroll
-        for (int k = 0; k <= TB; ++k) y[k] = yb[(TB - k) * SB_LD];
-        // window slot 0; slots whose column falls outside 0..ta have zero weight
+        for (int k = 0; k <= TB; ++k) {
+            y[k] = yb[(TB - k) * SB_LD];
+            ys[k] = make_float2(y[k].y, y[k].x);
+        }
         const float2* xb = ut + (ua + p1 * (ta + 1) + c0) * SB_LD + lane;
-        float tr[NC], ti[NC];
+        float2 S[NC], T[NC];
 #pragma unroll
-        for (int o = 0; o < NC; ++o) tr[o] = ti[o] = 0.f;
+        for (int o = 0; o < NC; ++o) S[o] = T[o] = make_float2(0.f, 0.f);
 #pragma unroll
         for (int w = 0; w < TB + NC; ++w) {
             const float2 x = xb[w * SB_LD];
@@ -177,24 +183,25 @@ __device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__
                 const int k = w - o;
                 if (k < 0 || k > TB) continue;
                 const float cc = c2[o * (TB + 1) + k];
-                const float pr = x.x * y[k].x - x.y * y[k].y;
-                const float pi = x.x * y[k].y + x.y * y[k].x;
-                tr[o] += cc * pr;
-                ti[o] += cc * pi;
+                const float2 cx = __fmul2_rn(make_float2(cc, cc), x);
+                S[o] = __ffma2_rn(cx, y[k], S[o]);
+                T[o] = __ffma2_rn(cx, ys[k], T[o]);
             }
         }
+        const float2 cc1 = make_float2(c1, c1);
 #pragma unroll
         for (int o = 0; o < NC; ++o) {
-            zr[o] += c1 * tr[o];
-            zi[o] += c1 * ti[o];
+            zS[o] = __ffma2_rn(cc1, S[o], zS[o]);
+            zT[o] = __ffma2_rn(cc1, T[o], zT[o]);
         }
     }
     const float be = beff[J.w >> 16];
     float2* out = yt + (J.w & 0xffff) * SB_LD + lane;
 #pragma unroll
     for (int o = 0; o < NC; ++o) {
+        const float zr = zS[o].x - zS[o].y, zi = zT[o].x + zT[o].y;
         const float2 v = out[o * SB_LD];
-        out[o * SB_LD] = make_float2(v.x + be * zr[o], v.y + be * zi[o]);
+        out[o * SB_LD] = make_float2(v.x + be * zr, v.y + be * zi);
     }
 }
 
