@@ -55,6 +55,26 @@ def _dist():
     return ws, rank, local
 
 
+def _shard(rank):
+    """Rank r owns the intervals [r*NSLAB, (r+1)*NSLAB) (their ids key the noise) and draws its own
+    configurations and lengths from a rank-specific seed: the ranks share no data."""
+    return 2212 + 7919 * rank, rank * NSLAB
+
+
+def _job_rate(elapsed_ms, atom_steps, ws, device):
+    """Whole-job throughput: atom-steps summed over the ranks / elapsed time maxed over the ranks.
+    Returns (rate per s, job elapsed ms, job atom-steps)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+        a = torch.tensor([atom_steps], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        elapsed_ms, atom_steps = float(t.item()), float(a.item())
+    return atom_steps / (elapsed_ms / 1e3), elapsed_ms, atom_steps
+
+
 class Clocks:
     """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
@@ -227,9 +247,10 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     lo, hi = (5, 20) if args.case == "small" else (100, 2000)
-    q, v, box, beta, L, ids = W.batch_workload(master=2212 + 7919 * rank, nbatch=NSLAB, T=TEMP, lo=lo, hi=hi)
+    master, id0 = _shard(rank)
+    q, v, box, beta, L, ids = W.batch_workload(master=master, nbatch=NSLAB, T=TEMP, lo=lo, hi=hi)
     n = q.shape[2]
-    ids = ids + rank * NSLAB
+    ids = ids + id0
     total_atom_steps = float(L.astype(np.int64).sum()) * n
     lp = P.langevin(dt=DT, gamma=GAMMA, T=TEMP, scheme=P.SCHEME_PAPER, schedule=P.SCHED_ROBUST, seed=2212)
     tq, tv = torch.as_tensor(q, device=dev), torch.as_tensor(v, device=dev)
@@ -295,12 +316,7 @@ def run_ours(args):
     clk = clocks.stop()
     eng.sync_status()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    tot_ms = float(np.sum(step_ms))
-    if ws > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = total_atom_steps * ws * args.steps / (tot_ms / 1e3)
+    value, tot_ms, job_atom_steps = _job_rate(float(np.sum(step_ms)), total_atom_steps * args.steps, ws, dev)
 
     # ---- roofline of the persistent SNAP kernel (FP32 ALU bound)
     per_pair, per_atom = P.Snap(P.snap_params(precision=P.FP32_BULK)).flop_model()
@@ -321,10 +337,11 @@ def run_ours(args):
            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
            "config": {"workload": WORKLOAD if args.case == "full" else SMALL, "precision": "FP32-bulk SNAP (FP64 sums, positions, noise)",
-                      "slabs_per_gpu": NSLAB, "atoms": n, "atom_steps_per_step": total_atom_steps * ws,
+                      "slabs_per_gpu": NSLAB, "atoms": n, "atom_steps_per_step": job_atom_steps / args.steps,
                       "l2": "flushed (256 MB write) before every timed step"},
            "roofline": roof, "clocks": clk, "gpu_launches": 3 * args.steps, "cuda_graph": graph_note}
-    out["parareal"] = _parareal(P, W, dev, torch)
+    if rank == 0:   # one-GPU extras (single-system parareal, FP64 form) run on rank 0 only
+        out["parareal"] = _parareal(P, W, dev, torch)
 
     # ---- matched force error FP32-bulk vs FP64 and the plain-FP64 form
     s64 = P.Snap(P.snap_params(precision=P.FP64))
@@ -333,7 +350,7 @@ def run_ours(args):
     _, F32, _ = P.snap_energy_forces(s32, tq, box, tbeta)
     ferr = float(((F32 - F64).abs().max() / F64.abs().max()).item())
     out["fp32_force_rel_err_vs_fp64"] = ferr
-    if not args.no_fp64:
+    if rank == 0 and not args.no_fp64:
         L64 = np.maximum(1, L // 20).astype(np.int32)
         e64 = P.Engine(n, box, P.snap_params(precision=P.FP64), P.fs_params(), beta=tbeta)
         e64.reserve(NSLAB)
@@ -354,7 +371,8 @@ def run_ours(args):
             ms64.append(a.elapsed_time(b))
         e64.sync_status()
         v64 = float(L64.sum()) * n / (np.mean(ms64) / 1e3)
-        out["fp64"] = {"value": v64, "unit": UNIT, "speedup_fp32_bulk": value / ws / v64,
+        out["fp64"] = {"value": v64, "unit": UNIT, "speedup_fp32_bulk": (total_atom_steps * args.steps / (
+                           float(np.sum(step_ms)) / 1e3)) / v64,
                        "sample": "same 64 intervals with L_b/20 steps (%d atom-steps)" % int(L64.sum() * n)}
 
     # ---- end to end through the C ABI from pinned host buffers
@@ -384,7 +402,10 @@ def run_ours(args):
     eng.sync_status()
     h2d = hq.numel() * 8 + hv.numel() * 8 + hL.numel() * 4 + hids.numel() * 8
     d2h = oq.numel() * 8 + ov.numel() * 8
-    out["e2e"] = {"value": total_atom_steps * ws / (np.mean(e2e_ms) / 1e3), "unit": UNIT,
+    if ws > 1:
+        torch.distributed.barrier()
+    e2e_value, _, _ = _job_rate(float(np.sum(e2e_ms)), total_atom_steps * len(e2e_ms), ws, dev)
+    out["e2e"] = {"value": e2e_value, "unit": UNIT,
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank == 0 and ws == 1 and not args.no_cpu:
