@@ -33,6 +33,22 @@ NSLAB, NCELL, TEMP, DT, GAMMA = 64, 4, 1500.0, 1e-3, 1.0
 WORKLOAD = ("batched fine propagation: 64 intervals x 129-atom W+SIA cell, SNAP 2J=8 (55 B, fitted to FS W), "
             "L_b ~ U{100..2000}, 1500 K, dt 1 fs, gamma 1/ps, one persistent launch")
 SMALL = "profiling case: the same 64 intervals with L_b ~ U{5..20}"
+# DRAM bytes (read + write) of one full-size launch of the persistent FP32 kernel, from one ncu
+# capture of this workload (profiles/fine_persistent_batch64_dram.md), valid only for the kernel
+# sources it was taken on (fingerprint of paper_2212_10508_gb300/csrc); reported as null otherwise.
+TRAFFIC = {"bytes_per_launch": 2.53e6 + 7.93e6, "csrc_sha256_16": "f5152460117c559e"}
+
+
+def _csrc_fingerprint():
+    import glob
+    import hashlib
+    d = os.path.join(ROOT, "paper_2212_10508_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(d + "/*.cu") + glob.glob(d + "/*.cuh") + glob.glob(d + "/*.h") + glob.glob(d + "/*.cpp")):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def _args():
@@ -329,7 +345,9 @@ def run_ours(args):
     sm_clock = 2070.0
     peak = 152 * 128 * 2 * sm_clock * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / peak, 4), "traffic": None,
+            "frac": round(achieved / peak, 4),
+            "traffic": TRAFFIC["bytes_per_launch"] if (args.case == "full" and
+                                                       _csrc_fingerprint() == TRAFFIC["csrc_sha256_16"]) else None,
             "kernel": "k_fine_persistent<float,8>", "kernel_ms": round(k_ms, 3),
             "flops_per_launch": flops, "peak_basis": "FP32 ALU: 152 SMs x 128 lanes x 2 flop x 2070 MHz"}
 
