@@ -26,7 +26,7 @@ constexpr int SB_ATOMS = 32;              // atoms per batch = lanes of the Y ph
 constexpr int SB_LD = 33;                 // leading dimension of the [element][atom] arrays
 constexpr int SB_WARPS = 16;
 constexpr int SB_THREADS = SB_WARPS * 32;
-constexpr int SB_CHUNK = 8;               // U-pass elements summed per lane-sum round
+constexpr int SB_CHUNK = 8;               // U-pass elements summed per lane-sum round (4 lanes each)
 constexpr int SB_SMALL_TB = 3;            // sub-block sizes tb <= this share one Y stage
 constexpr int SB_MAX_STAGES = 16;
 constexpr int SB_GUARD = 16;              // zero rows before and after U_tot (>= twojmax)
@@ -70,7 +70,10 @@ __host__ __device__ constexpr size_t sb_yt_elems() {
 
 // ---- U phase -----------------------------------------------------------------------------------
 // Sink of the U recursion: store w * U(g_k) of this lane; every SB_CHUNK elements (traversal
-// order) sum the stored values over the 32 lanes in a fixed order and add them to U_tot.
+// order) sum the stored values over the 32 lanes in a fixed order (per element: four partial
+// sums of 8 lanes, combined pairwise) and add them to U_tot.
+static_assert(SB_CHUNK == 8, "the lane sums map 8 elements x 4 quarters onto 32 lanes");
+
 template <int TJ>
 struct SinkUB {
     float2* lv;
@@ -87,16 +90,25 @@ struct SinkUB {
             constexpr int base = E - E % SB_CHUNK;
             constexpr int cnt = E - base + 1;
             __syncwarp();
-            if (lane < cnt) {
-                float sr = 0.f, si = 0.f;
-#pragma unroll 8
-                for (int j = 0; j < 32; ++j) {
-                    const float2 x = lv[lane * SB_LD + j];
+            // all 32 lanes: lane (e = lane & 7, quarter h = lane >> 3) sums neighbour lanes
+            // 8h..8h+7 of element e; the four quarters are combined by two xor-shuffles
+            const int e = lane & 7, h = lane >> 3;
+            float sr = 0.f, si = 0.f;
+            if (e < cnt) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float2 x = lv[e * SB_LD + 8 * h + j];
                     sr += x.x;
                     si += x.y;
                 }
-                // element base + lane in traversal order; identity on the diagonal (self term)
-                const ElemRT<float>& t = tab[base + lane];
+            }
+            sr += __shfl_xor_sync(0xffffffffu, sr, 8);
+            si += __shfl_xor_sync(0xffffffffu, si, 8);
+            sr += __shfl_xor_sync(0xffffffffu, sr, 16);
+            si += __shfl_xor_sync(0xffffffffu, si, 16);
+            if (h == 0 && e < cnt) {
+                // element base + e in traversal order; identity on the diagonal (self term)
+                const ElemRT<float>& t = tab[base + e];
                 float2* d = ut + t.full * SB_LD + slot;
                 if (first) {
                     *d = make_float2(sr + (t.diag ? 1.f : 0.f), si);

@@ -151,7 +151,8 @@ __device__ __forceinline__ void cayley_klein(const Vec4<real>& d, real kappa, re
 
 // Force on atom k of a system, one warp: F_k = sum_{j in N(k)} (dE_k/dr_kj - dE_j/dr_jk), with
 // neighbour lists sorted by index and symmetric.  Lane l handles the neighbour slots l and l + 32
-// of N(k) and finds the slot of k in N(j) by binary search (the searches of the lanes overlap);
+// of N(k) and finds the slot of k in N(j) by binary search (the searches of the lanes overlap;
+// loading j's whole row instead moved ~60 MB per step through L2 and was slower);
 // the per-lane partial sums are combined by a butterfly over the 32 lanes: a fixed order, and
 // every lane ends with the same bits.
 template <typename real>
