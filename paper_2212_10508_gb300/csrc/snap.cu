@@ -39,10 +39,22 @@ static double clebsch(int tj1, int tm1, int tj2, int tm2, int tJ, int tM) {
 // warps take rows from a shared counter, and a row's jobs of the stage run in a fixed order on the
 // warp that took it.  Each output's update sequence is therefore fixed (stages in order, then the
 // row's jobs in order) whatever warp runs it: the sums are deterministic.
+// Rows i of U^a that a job visits, [ilo, ihi] (p1 = p + s - tb + i within 0..ta).  In a diagonal
+// block (ta = tb) the rows i and i* = tb - p10 - i hold the same two factors swapped (p1 <-> p2, and
+// every column pair likewise), with the same product of Clebsch-Gordan weights (their two sign
+// factors (-1)^(a+b-J) cancel), so the two rows sum to the same value: the job visits i <= i* only
+// and weights i < i* twice.
+static void job_rows(int ta, int tb, int p10, int* ilo, int* ihi) {
+    *ilo = p10 < 0 ? -p10 : 0;
+    *ihi = std::min(tb, ta - p10);
+    if (ta == tb) *ihi = std::min(*ihi, (tb - p10) / 2);
+}
+
 // Coefficient record of one job (float offset, a multiple of 4, into T->sb_coef): first the
 // column weights c2[o][k] = <a q1, b tb-k | J q> with q = qlo + o, q1 = q + s - tb + k (zero where
 // q1 is outside 0..ta), o < h_ncol(J), k <= tb; then the row weights c1[i] = <a p1, b tb-i | J p>
-// with p1 = p + s - tb + i (zero outside 0..ta); padded to a multiple of 4.
+// with p1 = p + s - tb + i (zero outside 0..ta; doubled for the paired rows of a diagonal block);
+// padded to a multiple of 4.
 static int append_job_coefs(SnapHostTables* T, int blk, int tj, int p) {
     const int ta = T->blk_ta[blk], tb = T->blk_tb[blk], nc = ncol_half(tj);
     const double* cg = T->cg.data() + T->blk_cgoff[blk];
@@ -55,7 +67,8 @@ static int append_job_coefs(SnapHostTables* T, int blk, int tj, int p) {
         }
     for (int i = 0; i <= tb; ++i) {
         const int p1 = p10 + i;
-        T->sb_coef.push_back(p1 >= 0 && p1 <= ta ? (float)cg[p1 * (tb + 1) + (tb - i)] : 0.f);
+        const double w = (ta == tb && 2 * i < tb - p10) ? 2.0 : 1.0;
+        T->sb_coef.push_back(p1 >= 0 && p1 <= ta ? (float)(w * cg[p1 * (tb + 1) + (tb - i)]) : 0.f);
     }
     while (T->sb_coef.size() % 4) T->sb_coef.push_back(0.f);
     return off;
@@ -75,15 +88,11 @@ static void build_batch_jobs(SnapHostTables* T) {
                 if (T->blk_tj[id] != tj) continue;
                 const int ta = T->blk_ta[id], tb = T->blk_tb[id];
                 const int s = (ta + tb - tj) / 2, p10 = p + s - tb, c0 = qlo(tj) + s - tb;
-                int ni = 0;
-                for (int i = 0; i <= tb; ++i) ni += (p10 + i >= 0 && p10 + i <= ta);
-                if (!ni) continue;
-                int terms = 0, loads = tb + 1;
-                for (int w = 0; w < tb + nc; ++w) {
-                    if (c0 + w < 0 || c0 + w > ta) continue;
-                    ++loads;
-                    for (int o = 0; o < nc; ++o) terms += (w - o >= 0 && w - o <= tb);
-                }
+                int ilo, ihi;
+                job_rows(ta, tb, p10, &ilo, &ihi);
+                const int ni = ihi - ilo + 1;
+                if (ni <= 0) continue;
+                const int terms = nc * (tb + 1), loads = 2 * tb + nc + 1;   // branch-free windows
                 auto& row = stage[sb_stage_of(tb)][{tj, p}];
                 row.first += ni * (6.0 * terms + 2.0 * loads) + nc * (tb + 1) + 4.0 * nc + 20.0;
                 row.second.push_back({tj, p, id, ta, tb});
@@ -108,7 +117,9 @@ static void build_batch_jobs(SnapHostTables* T) {
             std::stable_sort(js.begin(), js.end(), [](const RJ& x, const RJ& y) { return x.tb < y.tb; });
             const int j0 = (int)T->sb_jobs.size() / 4;
             for (const RJ& j : js) {
-                T->sb_jobs.push_back(j.ta | (j.tb << 4) | (j.tj << 8) | (j.p << 12));
+                int ilo, ihi;
+                job_rows(j.ta, j.tb, j.p + (j.ta + j.tb - j.tj) / 2 - j.tb, &ilo, &ihi);
+                T->sb_jobs.push_back(j.ta | (j.tb << 4) | (j.tj << 8) | (j.p << 12) | (ilo << 16) | (ihi << 20));
                 T->sb_jobs.push_back(append_job_coefs(T, j.blk, j.tj, j.p));
                 T->sb_jobs.push_back(uoff_full(j.ta) | (uoff_full(j.tb) << 16));
                 T->sb_jobs.push_back((T->hoff[j.tj] + j.p * ncol_half(j.tj)) | (j.blk << 16));

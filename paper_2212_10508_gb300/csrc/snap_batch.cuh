@@ -144,7 +144,9 @@ __device__ __noinline__ void sb_u_round(float2* lv, float2* ut, const Vec4<float
 // (sm_100+ paired FMA): per term cx = c2 (xr, xi), S += cx * (yr, yi), T += cx * (yi, yr), so
 // that S = (sum c xr yr, sum c xi yi) and T = (sum c xr yi, sum c xi yr); each row's S and T are
 // scaled by its weight c1 and Z = (S.x - S.y, T.x + T.y) is formed once per job.
-// Job record: x = ta | tb << 4 | tj << 8 | p << 12; y = offset of the job's weights in coef
+// Job record: x = ta | tb << 4 | tj << 8 | p << 12 | ilo << 16 | ihi << 20 (rows i visited: all
+// valid rows, or in a diagonal block ta = tb only i <= i* = tb - p10 - i with the rows i < i*
+// weighted twice, since rows i and i* sum to the same value); y = offset of the job's weights in coef
 // (column weights c2[o][k], zero where q1 is out of range, then row weights c1[i]);
 // z = full offset of U^a | full offset of U^b << 16; w = half index of (tj, p, qlo) | blk << 16.
 template <int TB, int NC>
@@ -166,8 +168,7 @@ __device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__
         c2[4 * v + 3] = t.w;
     }
     const float* c1p = coef + J.y + N2;
-    const int ilo = p10 < 0 ? -p10 : 0;
-    const int ihi = ta - p10 < TB ? ta - p10 : TB;
+    const int ilo = (J.x >> 16) & 15, ihi = (J.x >> 20) & 15;   // rows visited (host: job_rows)
     const int ua = J.z & 0xffff, ub = J.z >> 16;
     // paired accumulators: zS = sum c1 c2 (xr yr, xi yi), zT = sum c1 c2 (xr yi, xi yr)
     float2 zS[NC], zT[NC];
