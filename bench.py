@@ -7,7 +7,8 @@ Workload (one "step"): 64 intervals of the 129-atom W + SIA cell (4^3 BCC cells 
 dumbbell), SNAP coefficients fitted to Finnis-Sinclair tungsten (tests/golden/beta_fs_w_2j8.txt;
 random coefficients collapse the cell), interval lengths L_b ~ U{100..2000}, 1500 K, dt = 1 fs, gamma = 1/ps, paper scheme with the robust
 temperature schedule; the whole batch is advanced by one baoab_propagate_batch(FINE) call
-(FP32-bulk SNAP: U/Z/Y in FP32, sums in FP64; FP64 positions, velocities and noise).
+(FP32-bulk SNAP: U/Z/Y in FP32, energy sums in FP64, force sums in double-float; FP64 positions,
+velocities and noise).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -354,7 +355,7 @@ def run_ours(args):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32", "data": "synthetic",
-           "config": {"workload": WORKLOAD if args.case == "full" else SMALL, "precision": "FP32-bulk SNAP (FP64 sums, positions, noise)",
+           "config": {"workload": WORKLOAD if args.case == "full" else SMALL, "precision": "FP32-bulk SNAP (FP64 energy sums, double-float force sums; FP64 positions, velocities, noise)",
                       "slabs_per_gpu": NSLAB, "atoms": n, "atom_steps_per_step": job_atom_steps / args.steps,
                       "l2": "flushed (256 MB write) before every timed step"},
            "roofline": roof, "clocks": clk, "gpu_launches": 3 * args.steps, "cuda_graph": graph_note}

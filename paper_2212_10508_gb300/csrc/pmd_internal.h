@@ -112,6 +112,8 @@ struct pmd_engine {
     pmd::DevBuf status;              // int status word + barrier words
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_vh, s_order, s_Ls, s_result;
     pmd::DevBuf s_noise;             // Gaussian increments of a parareal_correct window
+    pmd::DevBuf s_gstep;             // Gaussian increments of one fine sub-step [item][3] (FP32 path)
+    pmd::DevBuf s_pos;               // reverse neighbour slots [member][j][k] (uint8), natoms <= PMD_POS_TABLE_MAX_ATOMS
     int cap_batch = 0;
     int device = 0;
     int num_sms = 0;
@@ -122,3 +124,6 @@ struct pmd_engine {
 };
 
 struct pmd_adaptive;  // defined in adaptive.cpp
+
+// systems up to this size keep a table of reverse neighbour slots (natoms^2 bytes per member)
+constexpr int PMD_POS_TABLE_MAX_ATOMS = 2048;

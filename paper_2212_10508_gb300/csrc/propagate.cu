@@ -71,6 +71,8 @@ struct FineArgs {
     const int* Lmax;
     unsigned int* bar;
     int* status;
+    double* gstep;          // FP32 path: G_{ell} of the sub-step's items [item][3], drawn in phase A
+    unsigned char* pos;     // reverse-slot tables [member][n][n], or nullptr (binary search)
 };
 
 __global__ void k_fine_prologue(const int32_t* __restrict__ nsteps, int nbatch, int schedule, int* __restrict__ order,
@@ -122,10 +124,11 @@ __device__ __forceinline__ int active_members(const int* Ls, int nbatch, int ell
 }
 
 // Phase B of sub-step ell for the items it = first + r * stride, r < SB_B_GROUP, it < items, one
-// warp: the noise G_{ell,n} of all the group's atoms at once (lanes 2r and 2r+1 draw Philox
-// blocks 0 and 1 of atom r: G_x, G_y and G_z), the force gather of each atom (whole warp, lanes
-// = neighbour slots), and the Langevin update of all atoms at once (lane 3r + al advances
-// component al of atom r).  Positions and velocities are loaded before the gathers.
+// warp: the noise G_{ell,n} of all the group's atoms (FP32 path: drawn during phase A and read
+// from gstep; FP64 path: lanes 2r and 2r+1 draw Philox blocks 0 and 1 of atom r: G_x, G_y and
+// G_z), the force gather of each atom (whole warp, lanes = neighbour slots), and the Langevin
+// update of all atoms at once (lane 3r + al advances component al of atom r).  Positions and
+// velocities are loaded before the gathers.
 constexpr int SB_B_GROUP = 8;
 
 template <typename real>
@@ -137,7 +140,7 @@ __device__ __noinline__ void fine_phase_b(const FineArgs& a, long first, long st
     const int rn = lane >> 1, ru = lane / 3, al = lane - 3 * ru;
     const long itn = first + (long)rn * stride, itu = first + (long)ru * stride;
     double g0 = 0.0, g1 = 0.0;
-    if (rn < SB_B_GROUP && itn < items) {
+    if (sizeof(real) == 8 && rn < SB_B_GROUP && itn < items) {   // FP32 path: drawn in phase A
         const int m = a.order[itn / n], k = (int)(itn % n);
         const int L = a.nsteps[m] < 0 ? 0 : a.nsteps[m];
         if (Lp.scheme == PMD_SCHEME_PAPER || ell < L) {
@@ -163,19 +166,30 @@ __device__ __noinline__ void fine_phase_b(const FineArgs& a, long first, long st
     }
     // gathers, one atom at a time; lane 3r + al keeps component al of atom r
     double Fa = 0.0;
+    FF Ff{0.f, 0.f};
     for (int r = 0; r < SB_B_GROUP; ++r) {
         const long it = first + (long)r * stride;
         if (it >= items) break;
         const int m = a.order[it / n], k = (int)(it % n);
-        double F[3];
-        warp_gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n,
-                                (const real*)a.dedr + (long)m * n * NMAX * 3, k, lane, F, a.status);
-        if (ru == r) Fa = al == 0 ? F[0] : (al == 1 ? F[1] : F[2]);
+        const unsigned char* pos = a.pos ? a.pos + (size_t)m * n * n : nullptr;
+        if constexpr (sizeof(real) == 4) {   // double-float sums; hi + lo evaluated by the update lane
+            FF F[3];
+            warp_gather_force_ff(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n,
+                                 (const float*)a.dedr + (long)m * n * NMAX * 3, k, lane, F, a.status, pos, n);
+            if (ru == r) Ff = al == 0 ? F[0] : (al == 1 ? F[1] : F[2]);
+        } else {
+            double F[3];
+            warp_gather_force<real>(a.nbr + (long)m * n * NMAX, a.nnb + (long)m * n,
+                                    (const real*)a.dedr + (long)m * n * NMAX * 3, k, lane, F, a.status, pos, n);
+            if (ru == r) Fa = al == 0 ? F[0] : (al == 1 ? F[1] : F[2]);
+        }
     }
+    if (sizeof(real) == 4) Fa = (double)Ff.hi + (double)Ff.lo;
     // G of (ru, al): G_x, G_y from lane 2 ru, G_z from lane 2 ru + 1
     const int src = 2 * (ru < SB_B_GROUP ? ru : 0) + (al == 2 ? 1 : 0);
     const double s0 = __shfl_sync(0xffffffffu, g0, src), s1 = __shfl_sync(0xffffffffu, g1, src);
-    const double G = al == 1 ? s1 : s0;
+    double G = al == 1 ? s1 : s0;
+    if (sizeof(real) == 4 && upd) G = a.gstep[itu * 3 + al];
     double qn = qv;
     if (upd) {
         bool bad = false;
@@ -220,8 +234,34 @@ __device__ __noinline__ void fine_phase_b(const FineArgs& a, long first, long st
 }
 
 // Phase A of sub-step ell over the items (active member, atom) = [0, A n).
+// Draws G_{ell,n} of the batch's items [bs, bs + na) into gstep: task t = 32 w + lane of the first
+// warps, atom slot t / 2, Philox block t % 2 (block 0 gives G_x, G_y, block 1 G_z).
+struct FineNoiseSide {
+    const FineArgs* a;
+    long bs;
+    int na, ell;
+    __device__ void operator()(int warp, int lane) const {
+        const int t = warp * 32 + lane;
+        if (warp * 32 >= 2 * na || t >= 2 * na) return;
+        const int n = a->n;
+        const long it = bs + (t >> 1);
+        const int m = a->order[it / n], k = (int)(it % n), blk = t & 1;
+        const uint64_t un = (uint64_t)a->ids[m];
+        uint32_t c[4] = {2u * (uint32_t)k + (uint32_t)blk, (uint32_t)ell, (uint32_t)un, (uint32_t)(un >> 32)};
+        philox4x32_10(c, (uint32_t)a->L.seed, (uint32_t)(a->L.seed >> 32));
+        double g0, g1;
+        box_muller(c, g0, g1);
+        if (blk == 0) {
+            a->gstep[it * 3 + 0] = g0;
+            a->gstep[it * 3 + 1] = g1;
+        } else {
+            a->gstep[it * 3 + 2] = g0;
+        }
+    }
+};
+
 template <typename real, int TJ, class SH>
-__device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, long items, const double box[3]) {
+__device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, long items, const double box[3], int ell) {
     const int n = a.n;
     if constexpr (sizeof(real) == 4) {
         // batched design: CTA c takes the contiguous item range [c0, c1) in batches of 32 atoms
@@ -236,9 +276,12 @@ __device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, lo
                 const int i = (int)(it % n);
                 const long ai = m * n + i;
                 return SBAtom{a.q + m * a.stride, a.qf + m * n, i, a.nbr + ai * NMAX, a.nnb + ai,
-                              (float*)a.dedr + ai * NMAX * 3, nullptr};
+                              (float*)a.dedr + ai * NMAX * 3, nullptr,
+                              a.pos ? a.pos + ((size_t)m * n + i) * n : nullptr};
             };
-            sb_batch<TJ>(sh, a.v.sbjobs, a.v.sbrows, a.v.sbsptr, a.v.sbcoef, a.v.sp, na, at, n, box, a.status, true);
+            const FineNoiseSide side{&a, bs, na, ell};
+            sb_batch<TJ>(sh, a.v.sbjobs, a.v.sbrows, a.v.sbsptr, a.v.sbcoef, a.v.sp, na, at, n, box, a.status, true,
+                         side);
         }
     } else {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -267,7 +310,7 @@ __device__ __forceinline__ void fine_loop(const FineArgs& a, const SH& sh) {
         const int A = active_members(a.Ls, a.nbatch, ell);
         if (A == 0) break;
         const long items = (long)A * n;
-        fine_phase_a<real, TJ>(a, sh, items, box);
+        fine_phase_a<real, TJ>(a, sh, items, box, ell);
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
         for (long first = gwarp; first < items; first += (long)SB_B_GROUP * nwarps)
             fine_phase_b<real>(a, first, nwarps, items, ell, lane);
@@ -313,6 +356,8 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
     a.dedr = e->s_dedr.p;
     a.qf = e->s_qf.as<float4>();
     a.vh = e->s_vh.as<double>();
+    a.gstep = e->s_gstep.as<double>();
+    a.pos = n <= PMD_POS_TABLE_MAX_ATOMS && sizeof(real) == 4 ? e->s_pos.as<unsigned char>() : nullptr;
     a.order = e->s_order.as<int>();
     a.Ls = e->s_order.as<int>() + e->cap_batch;
     a.Lmax = e->s_order.as<int>() + 2 * e->cap_batch;

@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(snap_cta_threads<real>(), 1)
                 const long item = bs + slot;
                 const long bb = item / n;
                 return SBAtom{pos + bb * 3 * n, qf + bb * n, (int)(item % n), nbr + item * NMAX, nnb + item,
-                              dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr};
+                              dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr, nullptr};
             };
             sb_batch<TJ>(sh, v.sbjobs, v.sbrows, v.sbsptr, v.sbcoef, v.sp, na, at, n, box, status, want_forces != 0);
         }

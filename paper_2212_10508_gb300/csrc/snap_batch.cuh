@@ -68,6 +68,12 @@ __host__ __device__ constexpr size_t sb_yt_elems() {
     return a > b ? a : b;
 }
 
+// Extra work for idle FP64 pipes: called once per batch by every warp of the CTA at the start of
+// the largest Y stage, before the warp takes rows (the row counter balances the stage).
+struct SBNoSide {
+    __device__ void operator()(int, int) const {}
+};
+
 // ---- U phase -----------------------------------------------------------------------------------
 // Sink of the U recursion: store w * U(g_k) of this lane; every SB_CHUNK elements (traversal
 // order) sum the stored values over the 32 lanes in a fixed order (per element: four partial
@@ -247,15 +253,17 @@ __device__ __noinline__ void sb_y_row(const int4* __restrict__ jobs, int j0, int
 }
 
 // The whole Y phase of a batch (all threads of the CTA; ends with a CTA barrier).
-template <int TJ>
+template <int TJ, class Side = SBNoSide>
 __device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const int4* __restrict__ jobs,
                                            const int2* __restrict__ rows, const int* __restrict__ sptr,
-                                           const float* __restrict__ coef, int lane) {
+                                           const float* __restrict__ coef, int lane, const Side& side = Side()) {
+    constexpr int side_stage = sb_stage_of(TJ >= 6 ? 6 : TJ);
     for (int x = threadIdx.x; x < Dims<TJ>::NHALF * SB_LD; x += blockDim.x) sh.yt[x] = make_float2(0.f, 0.f);
     if (threadIdx.x < SB_MAX_STAGES) sh.ctr[threadIdx.x] = 0;
     __syncthreads();
     for (int st = 0; st < sb_num_stages(TJ); ++st) {   // stages of sub-block sizes
         const int r0 = sptr[st], r1 = sptr[st + 1];
+        if (st == side_stage) side(threadIdx.x >> 5, lane);
         if (r0 == r1) continue;
         for (;;) {
             int r = 0;
@@ -346,15 +354,17 @@ struct SBAtom {
     int* nnb_out;
     float* dedr_out;       // [NMAX][3]
     cplx<float>* utot_out; // [NFULL] or nullptr
+    unsigned char* pos_row;  // row i of the member's reverse-slot table (pos[i][j] = slot of j in N(i)), or nullptr
 };
+
 
 // All threads of the CTA call it with the same arguments.  at(slot) returns the SBAtom of the
 // batch's atom slot (slot < na).  Ends with a CTA barrier.
-template <int TJ, class AtomOf>
+template <int TJ, class AtomOf, class Side = SBNoSide>
 __device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, const int2* __restrict__ rows,
                          const int* __restrict__ sptr, const float* __restrict__ coef,
                          const SnapDevParams& sp, int na, const AtomOf& at, int n, const double box[3], int* status,
-                         bool want_forces) {
+                         bool want_forces, const Side& side = Side()) {
     constexpr int NH = Dims<TJ>::NHALF, NF = Dims<TJ>::NFULL;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float kappa = float(sp.rfac0 * PI / sp.rcut);
@@ -370,7 +380,10 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, 
         int* nb = sh.nbr + slot * NMAX;
         Vec4<float>* dp = sh.disp + slot * NMAX;
         const int cnt = warp_neighbors<float>(nb, dp, lane, n, A.i, A.q64, A.qf, box, sp.rcut, status);
-        for (int s = lane; s < cnt; s += 32) A.nbr_out[s] = nb[s];
+        for (int s = lane; s < cnt; s += 32) {
+            A.nbr_out[s] = nb[s];
+            if (A.pos_row) A.pos_row[nb[s]] = (unsigned char)s;
+        }
         if (lane == 0) {
             *A.nnb_out = cnt;
             sh.nnb[slot] = cnt;
@@ -398,7 +411,7 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, 
     __syncthreads();
     if (!want_forces) return;
 
-    sb_y_phase<TJ>(sh, jobs, rows, sptr, coef, lane);
+    sb_y_phase<TJ>(sh, jobs, rows, sptr, coef, lane, side);
 
     // dE/dr phase
     for (int slot = warp; slot < na; slot += SB_WARPS) {

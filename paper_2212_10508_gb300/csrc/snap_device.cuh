@@ -149,51 +149,119 @@ __device__ __forceinline__ void cayley_klein(const Vec4<real>& d, real kappa, re
     }
 }
 
+// Unevaluated float pair hi + lo (double-float arithmetic, Knuth's TwoSum / Dekker's Fast2Sum):
+// used to sum FP32 pair derivatives with FP64-class accuracy on the FP32 pipes.
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v));
+    return FF{s, e};   // s + e == a + b exactly
+}
+// Symmetric in its arguments (the exact error of hi + hi, then lo + lo, then one renormalisation),
+// so a butterfly leaves the same bits in every lane.
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = ff_two_sum(x.hi, y.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    const float hi = __fadd_rn(s.hi, e);
+    return FF{hi, __fsub_rn(e, __fsub_rn(hi, s.hi))};
+}
+__device__ __forceinline__ FF ff_shfl_xor(FF x, int m) {
+    return FF{__shfl_xor_sync(0xffffffffu, x.hi, m), __shfl_xor_sync(0xffffffffu, x.lo, m)};
+}
+
+// Slot of atom k in the index-sorted list of j (nbr row lj, cj entries), or -1: from the member's
+// slot table pos[j][k] when there is one (written with the lists; checked against the list), else
+// by binary search.
+__device__ __forceinline__ int reverse_slot(const int* __restrict__ lj, int cj, int j, int k,
+                                            const unsigned char* pos, int n) {
+    if (pos) {
+        const int c = pos[(size_t)j * n + k];
+        return (c < cj && lj[c] == k) ? c : -1;
+    }
+    int lo = 0, hi = cj - 1;
+    while (lo <= hi) {
+        const int mid = (lo + hi) >> 1;
+        const int v = lj[mid];
+        if (v == k) return mid;
+        if (v < k) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
 // Force on atom k of a system, one warp: F_k = sum_{j in N(k)} (dE_k/dr_kj - dE_j/dr_jk), with
 // neighbour lists sorted by index and symmetric.  Lane l handles the neighbour slots l and l + 32
-// of N(k) and finds the slot of k in N(j) by binary search (the searches of the lanes overlap;
-// loading j's whole row instead moved ~60 MB per step through L2 and was slower);
-// the per-lane partial sums are combined by a butterfly over the 32 lanes: a fixed order, and
-// every lane ends with the same bits.
-template <typename real>
-__device__ __forceinline__ void warp_gather_force(const int* __restrict__ nbr, const int* __restrict__ nnb,
-                                                  const real* __restrict__ dedr, int k, int lane, double F[3],
-                                                  int* status) {
+// of N(k) (the slot of k in N(j): reverse_slot); the per-lane partial sums are combined by a
+// butterfly over the 32 lanes: a fixed order, and every lane ends with the same bits.
+// FP32 pair derivatives: every difference is held exactly as a float pair and summed in
+// double-float arithmetic (F = hi + lo, evaluated in FP64 by the caller); FP64: plain FP64 sums.
+__device__ __forceinline__ void warp_gather_force_ff(const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                     const float* __restrict__ dedr, int k, int lane, FF F[3],
+                                                     int* status, const unsigned char* pos = nullptr, int n = 0) {
     const int ck = nnb[k];
     const int* lk = nbr + (size_t)k * NMAX;
-    const real* dk = dedr + (size_t)k * NMAX * 3;
-    double f[3] = {0.0, 0.0, 0.0};
+    const float* dk = dedr + (size_t)k * NMAX * 3;
+    FF f[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
     for (int s = lane; s < ck; s += 32) {
         const int j = lk[s];
         const int cj = nnb[j];
-        const int* lj = nbr + (size_t)j * NMAX;
-        int lo = 0, hi = cj - 1, t = -1;
-        while (lo <= hi) {
-            const int mid = (lo + hi) >> 1;
-            const int v = lj[mid];
-            if (v == k) {
-                t = mid;
-                break;
-            }
-            if (v < k) lo = mid + 1;
-            else hi = mid - 1;
-        }
+        const int t = reverse_slot(nbr + (size_t)j * NMAX, cj, j, k, pos, n);
         if (t < 0) flag(status, ST_BADNEIGH);
-        const real* dj = dedr + ((size_t)j * NMAX + (t < 0 ? 0 : t)) * 3;
+        const float* dj = dedr + ((size_t)j * NMAX + (t < 0 ? 0 : t)) * 3;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double g = (double)dk[s * 3 + a];
-            const double h = t < 0 ? 0.0 : (double)dj[a];
-            f[a] += g - h;
+            const float g = dk[s * 3 + a];
+            const float h = t < 0 ? 0.f : dj[a];
+            f[a] = ff_add(f[a], ff_two_sum(g, -h));
         }
     }
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) f[a] += __shfl_xor_sync(0xffffffffu, f[a], m);
+        for (int a = 0; a < 3; ++a) f[a] = ff_add(f[a], ff_shfl_xor(f[a], m));
     F[0] = f[0];
     F[1] = f[1];
     F[2] = f[2];
+}
+
+template <typename real>
+__device__ __forceinline__ void warp_gather_force(const int* __restrict__ nbr, const int* __restrict__ nnb,
+                                                  const real* __restrict__ dedr, int k, int lane, double F[3],
+                                                  int* status, const unsigned char* pos = nullptr, int n = 0) {
+    if constexpr (sizeof(real) == 4) {
+        FF f[3];
+        warp_gather_force_ff(nbr, nnb, dedr, k, lane, f, status, pos, n);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) F[a] = (double)f[a].hi + (double)f[a].lo;
+    } else {
+        const int ck = nnb[k];
+        const int* lk = nbr + (size_t)k * NMAX;
+        const real* dk = dedr + (size_t)k * NMAX * 3;
+        double f[3] = {0.0, 0.0, 0.0};
+        for (int s = lane; s < ck; s += 32) {
+            const int j = lk[s];
+            const int cj = nnb[j];
+            const int t = reverse_slot(nbr + (size_t)j * NMAX, cj, j, k, pos, n);
+            if (t < 0) flag(status, ST_BADNEIGH);
+            const real* dj = dedr + ((size_t)j * NMAX + (t < 0 ? 0 : t)) * 3;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double g = (double)dk[s * 3 + a];
+                const double h = t < 0 ? 0.0 : (double)dj[a];
+                f[a] += g - h;
+            }
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) f[a] += __shfl_xor_sync(0xffffffffu, f[a], m);
+        F[0] = f[0];
+        F[1] = f[1];
+        F[2] = f[2];
+    }
 }
 
 }  // namespace pmd
