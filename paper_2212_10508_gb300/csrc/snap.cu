@@ -50,15 +50,19 @@ static void job_rows(int ta, int tb, int p10, int* ilo, int* ihi) {
     if (ta == tb) *ihi = std::min(*ihi, (tb - p10) / 2);
 }
 
+// First output column of a row job: rows p > J of an integer J skip the middle column q = J (m = 0),
+// whose elements are mirror images of rows p < J: Y(p, J) = (-1)^(p-J) conj Y(2J - p, J).
+static int job_first_col(int tj, int p) { return (tj % 2 == 0 && 2 * p > tj) ? 1 : 0; }
+
 // Coefficient record of one job (float offset, a multiple of 4, into T->sb_coef): first the
-// column weights c2[o][k] = <a q1, b tb-k | J q> with q = qlo + o, q1 = q + s - tb + k (zero where
-// q1 is outside 0..ta), o < h_ncol(J), k <= tb; then the row weights c1[i] = <a p1, b tb-i | J p>
+// column weights c2[o][k] = <a q1, b tb-k | J q> with q = qlo + o0 + o, q1 = q + s - tb + k (zero
+// where q1 is outside 0..ta), o < h_ncol(J) - o0, k <= tb; then the row weights c1[i] = <a p1, b tb-i | J p>
 // with p1 = p + s - tb + i (zero outside 0..ta; doubled for the paired rows of a diagonal block);
 // padded to a multiple of 4.
-static int append_job_coefs(SnapHostTables* T, int blk, int tj, int p) {
-    const int ta = T->blk_ta[blk], tb = T->blk_tb[blk], nc = ncol_half(tj);
+static int append_job_coefs(SnapHostTables* T, int blk, int tj, int p, int o0) {
+    const int ta = T->blk_ta[blk], tb = T->blk_tb[blk], nc = ncol_half(tj) - o0;
     const double* cg = T->cg.data() + T->blk_cgoff[blk];
-    const int s = (ta + tb - tj) / 2, p10 = p + s - tb, c0 = qlo(tj) + s - tb;
+    const int s = (ta + tb - tj) / 2, p10 = p + s - tb, c0 = qlo(tj) + o0 + s - tb;
     const int off = (int)T->sb_coef.size();
     for (int o = 0; o < nc; ++o)
         for (int k = 0; k <= tb; ++k) {
@@ -82,12 +86,12 @@ static void build_batch_jobs(SnapHostTables* T) {
     const int nstage = sb_num_stages(T->twojmax);
     std::vector<std::map<std::pair<int, int>, std::pair<double, std::vector<RJ>>>> stage(nstage);
     for (int tj = 0; tj <= T->twojmax; ++tj) {
-        const int nc = ncol_half(tj);
         for (int p = 0; p <= tj; ++p)
             for (int id = 0; id < nblk; ++id) {
+                const int nc = ncol_half(tj) - job_first_col(tj, p);
                 if (T->blk_tj[id] != tj) continue;
                 const int ta = T->blk_ta[id], tb = T->blk_tb[id];
-                const int s = (ta + tb - tj) / 2, p10 = p + s - tb, c0 = qlo(tj) + s - tb;
+                const int s = (ta + tb - tj) / 2, p10 = p + s - tb;
                 int ilo, ihi;
                 job_rows(ta, tb, p10, &ilo, &ihi);
                 const int ni = ihi - ilo + 1;
@@ -119,10 +123,12 @@ static void build_batch_jobs(SnapHostTables* T) {
             for (const RJ& j : js) {
                 int ilo, ihi;
                 job_rows(j.ta, j.tb, j.p + (j.ta + j.tb - j.tj) / 2 - j.tb, &ilo, &ihi);
-                T->sb_jobs.push_back(j.ta | (j.tb << 4) | (j.tj << 8) | (j.p << 12) | (ilo << 16) | (ihi << 20));
-                T->sb_jobs.push_back(append_job_coefs(T, j.blk, j.tj, j.p));
+                const int o0 = job_first_col(j.tj, j.p);
+                T->sb_jobs.push_back(j.ta | (j.tb << 4) | (j.tj << 8) | (j.p << 12) | (ilo << 16) | (ihi << 20) |
+                                     (o0 << 24));
+                T->sb_jobs.push_back(append_job_coefs(T, j.blk, j.tj, j.p, o0));
                 T->sb_jobs.push_back(uoff_full(j.ta) | (uoff_full(j.tb) << 16));
-                T->sb_jobs.push_back((T->hoff[j.tj] + j.p * ncol_half(j.tj)) | (j.blk << 16));
+                T->sb_jobs.push_back((T->hoff[j.tj] + j.p * ncol_half(j.tj) + o0) | (j.blk << 16));
             }
             T->sb_rows.push_back(j0);
             T->sb_rows.push_back((int)T->sb_jobs.size() / 4);

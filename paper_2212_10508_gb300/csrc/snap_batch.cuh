@@ -150,9 +150,11 @@ __device__ __noinline__ void sb_u_round(float2* lv, float2* ut, const Vec4<float
 // (sm_100+ paired FMA): per term cx = c2 (xr, xi), S += cx * (yr, yi), T += cx * (yi, yr), so
 // that S = (sum c xr yr, sum c xi yi) and T = (sum c xr yi, sum c xi yr); each row's S and T are
 // scaled by its weight c1 and Z = (S.x - S.y, T.x + T.y) is formed once per job.
-// Job record: x = ta | tb << 4 | tj << 8 | p << 12 | ilo << 16 | ihi << 20 (rows i visited: all
-// valid rows, or in a diagonal block ta = tb only i <= i* = tb - p10 - i with the rows i < i*
-// weighted twice, since rows i and i* sum to the same value); y = offset of the job's weights in coef
+// Job record: x = ta | tb << 4 | tj << 8 | p << 12 | ilo << 16 | ihi << 20 | o0 << 24 (rows i
+// visited: all valid rows, or in a diagonal block ta = tb only i <= i* = tb - p10 - i with the rows
+// i < i* weighted twice, since rows i and i* sum to the same value; o0 = 1: the row's outputs start
+// at column qlo + 1, the middle column being filled from its mirror image); y = offset of the job's
+// weights in coef
 // (column weights c2[o][k], zero where q1 is out of range, then row weights c1[i]);
 // z = full offset of U^a | full offset of U^b << 16; w = half index of (tj, p, qlo) | blk << 16.
 template <int TB, int NC>
@@ -161,7 +163,7 @@ __device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__
     const int ta = J.x & 15, tj = (J.x >> 8) & 15, p = (J.x >> 12) & 15;
     const int s = (ta + TB - tj) >> 1;
     const int p10 = p + s - TB;
-    const int c0 = ((tj + 1) >> 1) + s - TB;
+    const int c0 = ((tj + 1) >> 1) + ((J.x >> 24) & 1) + s - TB;   // first output column qlo + o0
     constexpr int N2 = NC * (TB + 1), NV = (N2 + 3) / 4;
     float c2[NV * 4];
     const float4* cp = reinterpret_cast<const float4*>(coef + J.y);
@@ -231,7 +233,7 @@ __device__ __noinline__ void sb_y_row(const int4* __restrict__ jobs, int j0, int
     for (int j = j0; j < j1; ++j) {
         const int4 J = jobs[j];
         const int tb = (J.x >> 4) & 15, tj = (J.x >> 8) & 15;
-        const int nc = tj + 1 - ((tj + 1) >> 1);
+        const int nc = tj + 1 - ((tj + 1) >> 1) - ((J.x >> 24) & 1);
         switch (nc * 16 + tb) {
 #define PMD_SB_CASE(NC_, TB_)                                                         \
     case NC_ * 16 + TB_:                                                              \
@@ -275,6 +277,28 @@ __device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const int4* _
         }
         __syncthreads();
     }
+}
+
+// Middle column of integer J (q = J/2 in doubled units, m = 0): rows p > J/2 are not computed by
+// the Y jobs; Y(p, q) = (-1)^(p-q) conj Y(tj - p, q).  All threads; ends with a CTA barrier.
+template <int TJ>
+__device__ __forceinline__ void sb_fill_middle(float2* yt) {
+    constexpr int NFILL = (TJ / 2) * (TJ / 2 + 1) / 2;   // sum over even tj <= TJ of tj / 2
+    for (int x = threadIdx.x; x < NFILL * SB_ATOMS; x += blockDim.x) {
+        const int atom = x % SB_ATOMS;
+        int f = x / SB_ATOMS, tj = 2;
+        while (f >= tj / 2) {
+            f -= tj / 2;
+            tj += 2;
+        }
+        const int q = tj / 2, p = q + 1 + f;
+        const int nc = tj + 1 - (tj + 1) / 2;
+        const int dst = h_off(tj) + p * nc, src = h_off(tj) + (tj - p) * nc;   // column q = qlo: offset 0
+        const float2 v = yt[src * SB_LD + atom];
+        const float sg = ((p - q) & 1) ? -1.f : 1.f;
+        yt[dst * SB_LD + atom] = make_float2(sg * v.x, -sg * v.y);
+    }
+    __syncthreads();
 }
 
 // ---- dE/dr phase -------------------------------------------------------------------------------
@@ -412,6 +436,7 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, 
     if (!want_forces) return;
 
     sb_y_phase<TJ>(sh, jobs, rows, sptr, coef, lane, side);
+    sb_fill_middle<TJ>(sh.yt);
 
     // dE/dr phase
     for (int slot = warp; slot < na; slot += SB_WARPS) {
