@@ -116,6 +116,8 @@ struct SinkUB {
                 // element base + e in traversal order; identity on the diagonal (self term)
                 const ElemRT<float>& t = tab[base + e];
                 float2* d = ut + t.full * SB_LD + slot;
+                sr *= t.nrm;   // V -> U
+                si *= t.nrm;
                 if (first) {
                     *d = make_float2(sr + (t.diag ? 1.f : 0.f), si);
                 } else {
@@ -316,9 +318,11 @@ __device__ __forceinline__ void sb_weight_y(const float2* yt, int slot, float2* 
             ym = yt[t.ymH * SB_LD + slot];
             if (t.ymMode != 0) ym = make_float2(t.ymMode * ym.x, -t.ymMode * ym.y);
         }
-        yw[e] = make_float2(t.wS * y0.x, t.wS * y0.y);
-        yw[NH + e] = make_float2(t.wP * yp.x, t.wP * yp.y);
-        yw[2 * NH + e] = make_float2(t.wQ * ym.x, t.wQ * ym.y);
+        // weights times nrm: the dE/dr pass contracts with V = U / nrm
+        const float wS = t.wS * t.nrm, wP = t.wP * t.nrm, wQ = t.wQ * t.nrm;
+        yw[e] = make_float2(wS * y0.x, wS * y0.y);
+        yw[NH + e] = make_float2(wP * yp.x, wP * yp.y);
+        yw[2 * NH + e] = make_float2(wQ * ym.x, wQ * ym.y);
     }
 }
 

@@ -37,13 +37,20 @@ struct HM {
     int hidx;         // row-major half index (Y half storage and job outputs)
     int src1, src2;   // traversal indices of the recursion sources (-1: zero coefficient)
     int yrule;        // 1: m = 0 column (b, conj a); 0: (a, -conj b)
-    double c1, c2;
+    double c1, c2;    // coefficients of the U recursion (the kernels run the V recursion: 1, 1)
+    double nrm;       // U = nrm * V, nrm = sqrt(p! (tj-p)! / (q! (tj-q)!))
     int full, mir, mirneg;
     double wD, wP, wQ, wS;
     int yp, ym;       // full indices of (p, q+1), (p, q-1) (-1: zero weight)
 };
 
 __host__ __device__ constexpr int trav(int tj, int p, int q) { return h_off(tj) + (q - h_qlo(tj)) * (tj + 1) + p; }
+
+__host__ __device__ constexpr double cfact(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
 
 __host__ __device__ constexpr HM hm(int E) {
     HM m{};
@@ -82,6 +89,7 @@ __host__ __device__ constexpr HM hm(int E) {
             }
         }
     }
+    m.nrm = csqrt(cfact(p) * cfact(tj - p) / (cfact(q) * cfact(tj - q)));
     m.full = f_off(tj) + p * (tj + 1) + q;
     m.mir = 2 * q > tj ? f_off(tj) + (tj - p) * (tj + 1) + (tj - q) : -1;
     m.mirneg = ((p - q) & 1) != 0;
@@ -112,6 +120,11 @@ struct ForE<N, N> {
 };
 
 // ---- per-lane recursion -------------------------------------------------------------------------
+// The recursion runs on V^j_{pq} = U^j_{pq} / nrm_{pq} with nrm_{pq} = sqrt(p! (tj-p)! / (q! (tj-q)!))
+// (p = j + m', q = j + m): the square-root coefficients of the U recursion are exactly absorbed, so
+// V^j_{pq} = A1 V^{j-1/2}_{src1} + A2 V^{j-1/2}_{src2} with unit weights (V^0 = 1).  The sinks
+// receive V; U = nrm V is applied once per atom (to the lane sums of U_tot, and folded into the
+// weighted copies of Y that the dE/dr pass contracts with V).
 template <typename real, int TJ, class Sink>
 struct URec {
     cplx<real> u[Dims<TJ>::NHALF];
@@ -130,15 +143,11 @@ struct URec {
             const cplx<real> A1 = m.yrule ? b : a;
             const cplx<real> A2 = m.yrule ? ca : mcb;
             cplx<real> v{real(0), real(0)};
-            if constexpr (m.src1 >= 0) {
-                const cplx<real> t = cmul(A1, u[m.src1 >= 0 ? m.src1 : 0]);
-                v.re += real(m.c1) * t.re;
-                v.im += real(m.c1) * t.im;
-            }
+            if constexpr (m.src1 >= 0) v = cmul(A1, u[m.src1 >= 0 ? m.src1 : 0]);
             if constexpr (m.src2 >= 0) {
-                const cplx<real> t = cmul(A2, u[m.src2 >= 0 ? m.src2 : 0]);
-                v.re += real(m.c2) * t.re;
-                v.im += real(m.c2) * t.im;
+                const cplx<real> x = u[m.src2 >= 0 ? m.src2 : 0];
+                v.re += A2.re * x.re - A2.im * x.im;
+                v.im += A2.re * x.im + A2.im * x.re;
             }
             u[E] = v;
         }
@@ -155,6 +164,7 @@ struct ElemRT {
     int full, mir, hidx, yp, ym, mirneg, diag;
     int ypH, ymH, ymMode;
     real wD, wP, wQ, wS;
+    real nrm;   // U = nrm * V of the recursion
 };
 
 template <typename real, int TJ>
@@ -173,7 +183,7 @@ __device__ inline void fill_elem_table(ElemRT<real>* tab) {
             }
         }
         tab[e] = ElemRT<real>{m.full, m.mir, m.hidx, m.yp, m.ym, m.mirneg, m.p == m.q ? 1 : 0, ypH, ymH, ymMode,
-                              real(m.wD), real(m.wP), real(m.wQ), real(m.wS)};
+                              real(m.wD), real(m.wP), real(m.wQ), real(m.wS), real(m.nrm)};
     }
 }
 
@@ -218,6 +228,8 @@ struct SinkU {
                 // element base + lane in traversal order; identity on the diagonal (self term)
                 const ElemRT<real>& t = tab[base + lane];
                 const int f = t.full;
+                sr *= t.nrm;   // V -> U
+                si *= t.nrm;
                 if (first) {
                     ws.full[f] = {sr + (t.diag ? real(1) : real(0)), si};
                 } else {
@@ -363,12 +375,14 @@ __device__ __forceinline__ void weight_y(const cplx<real>* full, cplx<real>* yw,
     for (int e = lane; e < NH; e += 32) {
         const ElemRT<real>& t = tab[e];
         const cplx<real> y0 = full[t.full];
-        yw[e] = {t.wD * y0.re, t.wD * y0.im};
-        yw[NH + e] = {t.wS * y0.re, t.wS * y0.im};
+        // weights times nrm: the dE/dr pass contracts with V = U / nrm
+        const real wD = t.wD * t.nrm, wS = t.wS * t.nrm, wP = t.wP * t.nrm, wQ = t.wQ * t.nrm;
+        yw[e] = {wD * y0.re, wD * y0.im};
+        yw[NH + e] = {wS * y0.re, wS * y0.im};
         const cplx<real> yp = full[t.yp >= 0 ? t.yp : t.full];
         const cplx<real> ym = full[t.ym >= 0 ? t.ym : t.full];
-        yw[2 * NH + e] = {t.wP * yp.re, t.wP * yp.im};
-        yw[3 * NH + e] = {t.wQ * ym.re, t.wQ * ym.im};
+        yw[2 * NH + e] = {wP * yp.re, wP * yp.im};
+        yw[3 * NH + e] = {wQ * ym.re, wQ * ym.im};
     }
 }
 
