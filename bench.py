@@ -37,7 +37,7 @@ SMALL = "profiling case: the same 64 intervals with L_b ~ U{5..20}"
 # DRAM bytes (read + write) of one full-size launch of the persistent FP32 kernel, from one ncu
 # capture of this workload (profiles/fine_persistent_batch64_dram.md), valid only for the kernel
 # sources it was taken on (fingerprint of paper_2212_10508_gb300/csrc); reported as null otherwise.
-TRAFFIC = {"bytes_per_launch": 2.53e6 + 7.93e6, "csrc_sha256_16": "f5152460117c559e"}
+TRAFFIC = {"bytes_per_launch": 3.72e6 + 346.43e6, "csrc_sha256_16": "605e1c87d686a345"}
 
 
 def _csrc_fingerprint():
