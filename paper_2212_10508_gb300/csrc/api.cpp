@@ -149,7 +149,8 @@ int pmd_snap_destroy(pmd_snap* s) {
     if (!s) return PMD_OK;
     DevBuf* bufs[] = {&s->d_cg, &s->d_blk, &s->d_beffptr, &s->d_befft, &s->d_beffc, &s->d_jobs,
                       &s->d_roundtb, &s->d_triblk, &s->s_nbr, &s->s_nnb, &s->s_dedr, &s->s_qf, &s->s_utot,
-                      &s->s_B, &s->s_status, &s->d_sbjobs, &s->d_sbrows, &s->d_sbsptr, &s->d_sbcoef};
+                      &s->s_B, &s->s_status, &s->d_sbjobs, &s->d_sbrows, &s->d_sbsptr, &s->d_sbcoef,
+                      &s->d_sbgroups, &s->d_sbgptr};
     for (DevBuf* b : bufs) b->release();
     delete s;
     return PMD_OK;

@@ -65,6 +65,8 @@ struct SnapHostTables {
     std::vector<int> sb_jobs;         // [njobs][4]
     std::vector<int> sb_rows;         // [nrows][2] job range of each (stage, row), stages concatenated
     std::vector<int> sb_sptr;         // [nstages + 1] row ranges of the stages
+    std::vector<int> sb_groups;       // [ngroups][2] (first row, count): equal-width rows, 2 or 4 per group
+    std::vector<int> sb_gptr;         // [2][nstages][2] group ranges [begin, end) per stage (R = 2, then R = 4)
     std::vector<float> sb_coef;       // per-job Clebsch-Gordan weights (column, then row)
     double sb_load_max = 0, sb_load_avg = 0;
     // bispectrum jobs (energy path): per triple t the block id of (j1, j2, j)
@@ -100,6 +102,8 @@ struct pmd_snap {
     pmd::DevBuf d_sbrows;    // int2 job range per (stage, row)
     pmd::DevBuf d_sbsptr;    // int [nstages + 1]
     pmd::DevBuf d_sbcoef;    // float per-job Clebsch-Gordan weights
+    pmd::DevBuf d_sbgroups;  // int2 row groups for multi-row warps
+    pmd::DevBuf d_sbgptr;    // int [2][nstages][2]
     // scratch
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_utot, s_B, s_status;
     int cap_atoms = 0;

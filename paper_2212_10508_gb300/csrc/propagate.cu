@@ -280,8 +280,7 @@ __device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, lo
                               a.pos ? a.pos + ((size_t)m * n + i) * n : nullptr};
             };
             const FineNoiseSide side{&a, bs, na, ell};
-            sb_batch<TJ>(sh, a.v.sbjobs, a.v.sbrows, a.v.sbsptr, a.v.sbcoef, a.v.sp, na, at, n, box, a.status, true,
-                         side);
+            sb_batch<TJ>(sh, sb_tables(a.v), a.v.sp, na, at, n, box, a.status, true, side);
         }
     } else {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

@@ -106,12 +106,21 @@ static void build_batch_jobs(SnapHostTables* T) {
     T->sb_rows.clear();
     T->sb_coef.clear();
     T->sb_sptr.assign(nstage + 1, 0);
+    T->sb_groups.clear();
+    T->sb_gptr.assign(2 * nstage * 2, 0);
     T->sb_load_max = 0.0;
     T->sb_load_avg = 0.0;
     for (int st = 0; st < nstage; ++st) {
+        // rows by decreasing width (outputs per row), then decreasing cost: the costly rows first, and
+        // rows of equal width adjacent (groups of 2 or 4 rows for multi-row warps)
         std::vector<std::pair<double, std::pair<int, int>>> rows;
         for (auto& kv : stage[st]) rows.push_back({kv.second.first, kv.first});
-        std::stable_sort(rows.begin(), rows.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        auto width = [](const std::pair<int, int>& r) { return ncol_half(r.first) - job_first_col(r.first, r.second); };
+        std::stable_sort(rows.begin(), rows.end(), [&](const auto& x, const auto& y) {
+            const int wx = width(x.second), wy = width(y.second);
+            return wx != wy ? wx > wy : x.first > y.first;
+        });
+        const int row0 = (int)T->sb_rows.size() / 2;
         // expected makespan of the greedy take-next order (for the record)
         std::vector<double> load(SB_WARPS, 0.0);
         for (auto& r : rows) {
@@ -134,6 +143,19 @@ static void build_batch_jobs(SnapHostTables* T) {
             T->sb_rows.push_back((int)T->sb_jobs.size() / 4);
         }
         T->sb_sptr[st + 1] = (int)T->sb_rows.size() / 2;
+        // row groups for multi-row warps (R = 2 and 4 rows of equal width per warp pass)
+        for (int g = 0; g < 2; ++g) {
+            const int R = g == 0 ? 2 : 4;
+            T->sb_gptr[(g * nstage + st) * 2] = (int)T->sb_groups.size() / 2;
+            for (size_t r = 0; r < rows.size();) {
+                size_t e = r + 1;
+                while (e < rows.size() && (int)(e - r) < R && width(rows[e].second) == width(rows[r].second)) ++e;
+                T->sb_groups.push_back(row0 + (int)r);
+                T->sb_groups.push_back((int)(e - r));
+                r = e;
+            }
+            T->sb_gptr[(g * nstage + st) * 2 + 1] = (int)T->sb_groups.size() / 2;
+        }
         double tot = 0.0;
         for (double x : load) tot += x;
         T->sb_load_max += *std::max_element(load.begin(), load.end());
@@ -339,6 +361,10 @@ static int upload_tables(pmd_snap* s) {
     PMD_CUDA_TRY(cudaMemcpy(s->d_sbcoef.p, T.sb_coef.data(), T.sb_coef.size() * sizeof(float), cudaMemcpyHostToDevice));
     if ((rc = s->d_sbrows.ensure(std::max<size_t>(1, T.sb_rows.size()) * sizeof(int)))) return rc;
     PMD_CUDA_TRY(cudaMemcpy(s->d_sbrows.p, T.sb_rows.data(), T.sb_rows.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbgroups.ensure(std::max<size_t>(2, T.sb_groups.size()) * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbgroups.p, T.sb_groups.data(), T.sb_groups.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if ((rc = s->d_sbgptr.ensure(T.sb_gptr.size() * sizeof(int)))) return rc;
+    PMD_CUDA_TRY(cudaMemcpy(s->d_sbgptr.p, T.sb_gptr.data(), T.sb_gptr.size() * sizeof(int), cudaMemcpyHostToDevice));
     if ((rc = s->d_sbsptr.ensure(T.sb_sptr.size() * sizeof(int)))) return rc;
     PMD_CUDA_TRY(cudaMemcpy(s->d_sbsptr.p, T.sb_sptr.data(), T.sb_sptr.size() * sizeof(int), cudaMemcpyHostToDevice));
     std::vector<int4> tb(T.nB);
@@ -368,6 +394,8 @@ SnapView snap_view(const pmd_snap* s, const double* beta) {
     v.sbrows = s->d_sbrows.as<int2>();
     v.sbcoef = s->d_sbcoef.as<float>();
     v.sbsptr = s->d_sbsptr.as<int>();
+    v.sbgroups = s->d_sbgroups.as<int2>();
+    v.sbgptr = s->d_sbgptr.as<int>();
     v.beta = beta;
     v.ncg = (int)s->T.cg.size();
     v.nblk = (int)s->T.blk_ta.size();
@@ -418,7 +446,7 @@ __global__ void __launch_bounds__(snap_cta_threads<real>(), 1)
                 return SBAtom{pos + bb * 3 * n, qf + bb * n, (int)(item % n), nbr + item * NMAX, nnb + item,
                               dedr + item * NMAX * 3, utot ? utot + item * Dims<TJ>::NFULL : nullptr, nullptr};
             };
-            sb_batch<TJ>(sh, v.sbjobs, v.sbrows, v.sbsptr, v.sbcoef, v.sp, na, at, n, box, status, want_forces != 0);
+            sb_batch<TJ>(sh, sb_tables(v), v.sp, na, at, n, box, status, want_forces != 0);
         }
     } else {
         SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, v);

@@ -74,6 +74,16 @@ struct SBNoSide {
     __device__ void operator()(int, int) const {}
 };
 
+// Device tables of the batched Y contraction.
+struct SBTables {
+    const int4* jobs;     // job records
+    const int2* rows;     // job range of each (stage, row)
+    const int* sptr;      // row ranges of the stages
+    const float* coef;    // per-job Clebsch-Gordan weights
+    const int2* groups;   // (first row, count) groups of equal-width rows
+    const int* gptr;      // [2][nstages][2] group ranges [begin, end) per stage, for 2 and 4 rows per warp pass
+};
+
 // ---- U phase -----------------------------------------------------------------------------------
 // Sink of the U recursion: store w * U(g_k) of this lane; every SB_CHUNK elements (traversal
 // order) sum the stored values over the 32 lanes in a fixed order (per element: four partial
@@ -228,6 +238,120 @@ __device__ __forceinline__ void sb_yjob(const int4 J, const float2* __restrict__
     }
 }
 
+// The same contraction for a warp whose sub-warps of 32/R lanes each run a job of a different row
+// (few atoms: lane la = lane % (32/R) of sub-warp lane / (32/R) is atom la).  The job parameters
+// are per lane; all sub-warps run the same (TB, NC) variant, the row loop covers the union of the
+// sub-warps' row ranges, and a lane outside its own range reads row 0 (clamped) with zero weight.
+// Each output receives exactly the operations of the one-row form, in the same order.
+template <int TB, int NC>
+__device__ __forceinline__ void sb_yjob_m(const int4 J, bool valid, const float2* __restrict__ ut,
+                                          const float* __restrict__ coef, const float* __restrict__ beff,
+                                          float2* __restrict__ yt, int la) {
+    const int ta = J.x & 15, tj = (J.x >> 8) & 15, p = (J.x >> 12) & 15;
+    const int ilo = valid ? (J.x >> 16) & 15 : TB + 1, ihi = valid ? (J.x >> 20) & 15 : -1;
+    const int s = (ta + TB - tj) >> 1;
+    const int p10 = p + s - TB;
+    const int c0 = ((tj + 1) >> 1) + ((J.x >> 24) & 1) + s - TB;
+    constexpr int N2 = NC * (TB + 1), NV = (N2 + 3) / 4;
+    float c2[NV * 4];
+    const float4* cp = reinterpret_cast<const float4*>(coef + (valid ? J.y : 0));
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const float4 t = __ldg(cp + v);
+        c2[4 * v] = t.x;
+        c2[4 * v + 1] = t.y;
+        c2[4 * v + 2] = t.z;
+        c2[4 * v + 3] = t.w;
+    }
+    const float* c1p = coef + (valid ? J.y : 0) + N2;
+    const int wlo = __reduce_min_sync(0xffffffffu, ilo), whi = __reduce_max_sync(0xffffffffu, ihi);
+    const int ua = J.z & 0xffff, ub = J.z >> 16;
+    float2 zS[NC], zT[NC];
+#pragma unroll
+    for (int o = 0; o < NC; ++o) zS[o] = zT[o] = make_float2(0.f, 0.f);
+    for (int i = wlo; i <= whi; ++i) {
+        const bool on = i >= ilo && i <= ihi;
+        const int p1 = on ? p10 + i : 0;
+        const float c1 = on ? __ldg(c1p + i) : 0.f;
+        const float2* yb = ut + (ub + (TB - i) * (TB + 1)) * SB_LD + la;
+        float2 y[TB + 1], ys[TB + 1];
+#pragma unroll
+        for (int k = 0; k <= TB; ++k) {
+            y[k] = yb[(TB - k) * SB_LD];
+            ys[k] = make_float2(y[k].y, y[k].x);
+        }
+        const float2* xb = ut + (ua + p1 * (ta + 1) + c0) * SB_LD + la;
+        float2 S[NC], T[NC];
+#pragma unroll
+        for (int o = 0; o < NC; ++o) S[o] = T[o] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int w = 0; w < TB + NC; ++w) {
+            const float2 x = xb[w * SB_LD];
+#pragma unroll
+            for (int o = 0; o < NC; ++o) {
+                const int k = w - o;
+                if (k < 0 || k > TB) continue;
+                const float cc = c2[o * (TB + 1) + k];
+                const float2 cx = __fmul2_rn(make_float2(cc, cc), x);
+                S[o] = __ffma2_rn(cx, y[k], S[o]);
+                T[o] = __ffma2_rn(cx, ys[k], T[o]);
+            }
+        }
+        if (on) {
+            const float2 cc1 = make_float2(c1, c1);
+#pragma unroll
+            for (int o = 0; o < NC; ++o) {
+                zS[o] = __ffma2_rn(cc1, S[o], zS[o]);
+                zT[o] = __ffma2_rn(cc1, T[o], zT[o]);
+            }
+        }
+    }
+    if (valid) {
+        const float be = beff[J.w >> 16];
+        float2* out = yt + (J.w & 0xffff) * SB_LD + la;
+#pragma unroll
+        for (int o = 0; o < NC; ++o) {
+            const float zr = zS[o].x - zS[o].y, zi = zT[o].x + zT[o].y;
+            const float2 v = out[o * SB_LD];
+            out[o * SB_LD] = make_float2(v.x + be * zr, v.y + be * zi);
+        }
+    }
+}
+
+// One warp pass over a group of cnt <= R rows of equal width and one sub-block size TB (a stage
+// b >= 4): sub-warp r runs the jobs of row first + r, in order.
+template <int TJ>
+__device__ __noinline__ void sb_y_group(const SBTables tb, int2 G, int R, const float2* ut, const float* beff,
+                                        float2* yt, int lane) {
+    const int per = 32 / R, sub = lane / per, la = lane - sub * per;
+    const bool have = sub < G.y;
+    const int2 rj = have ? tb.rows[G.x + sub] : make_int2(0, 0);
+    const int len = rj.y - rj.x;
+    const int maxlen = __reduce_max_sync(0xffffffffu, len);
+    const int4 J0 = tb.jobs[tb.rows[G.x].x];   // sub-warp 0's first job fixes the variant
+    const int tbs = (J0.x >> 4) & 15, tj0 = (J0.x >> 8) & 15;
+    const int nc = tj0 + 1 - ((tj0 + 1) >> 1) - ((J0.x >> 24) & 1);
+    for (int t = 0; t < maxlen; ++t) {
+        const bool valid = have && t < len;
+        const int4 J = valid ? tb.jobs[rj.x + t] : J0;
+        switch (nc * 16 + tbs) {
+#define PMD_SBM_CASE(NC_, TB_)                                                                             \
+    case NC_ * 16 + TB_:                                                                                   \
+        if constexpr (TB_ <= TJ && NC_ <= h_ncol(TJ)) sb_yjob_m<TB_, NC_>(J, valid, ut, tb.coef, beff, yt, la); \
+        break;
+#define PMD_SBM_ROW(NC_) PMD_SBM_CASE(NC_, 4) PMD_SBM_CASE(NC_, 5) PMD_SBM_CASE(NC_, 6) PMD_SBM_CASE(NC_, 7) PMD_SBM_CASE(NC_, 8)
+            PMD_SBM_ROW(1)
+            PMD_SBM_ROW(2)
+            PMD_SBM_ROW(3)
+            PMD_SBM_ROW(4)
+            PMD_SBM_ROW(5)
+#undef PMD_SBM_ROW
+#undef PMD_SBM_CASE
+            default: break;
+        }
+    }
+}
+
 // Jobs [j0, j1) of one row, in order.
 template <int TJ>
 __device__ __noinline__ void sb_y_row(const int4* __restrict__ jobs, int j0, int j1, const float2* ut,
@@ -258,10 +382,14 @@ __device__ __noinline__ void sb_y_row(const int4* __restrict__ jobs, int j0, int
 
 // The whole Y phase of a batch (all threads of the CTA; ends with a CTA barrier).
 template <int TJ, class Side = SBNoSide>
-__device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const int4* __restrict__ jobs,
-                                           const int2* __restrict__ rows, const int* __restrict__ sptr,
-                                           const float* __restrict__ coef, int lane, const Side& side = Side()) {
+__device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const SBTables& tb, int lane, int na = SB_ATOMS,
+                                           const Side& side = Side()) {
     constexpr int side_stage = sb_stage_of(TJ >= 6 ? 6 : TJ);
+    constexpr int NST = sb_num_stages(TJ);
+    const int2* __restrict__ rows = tb.rows;
+    const int* __restrict__ sptr = tb.sptr;
+    // rows per warp pass: 4 sub-warps of 8 lanes for <= 8 atoms, 2 of 16 for <= 16 (stages b >= 4)
+    const int R = na <= 8 ? 4 : (na <= 16 ? 2 : 1);
     for (int x = threadIdx.x; x < Dims<TJ>::NHALF * SB_LD; x += blockDim.x) sh.yt[x] = make_float2(0.f, 0.f);
     if (threadIdx.x < SB_MAX_STAGES) sh.ctr[threadIdx.x] = 0;
     __syncthreads();
@@ -269,13 +397,25 @@ __device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const int4* _
         const int r0 = sptr[st], r1 = sptr[st + 1];
         if (st == side_stage) side(threadIdx.x >> 5, lane);
         if (r0 == r1) continue;
-        for (;;) {
-            int r = 0;
-            if (lane == 0) r = atomicAdd(&sh.ctr[st], 1);
-            r = r0 + __shfl_sync(0xffffffffu, r, 0);
-            if (r >= r1) break;
-            const int2 R = rows[r];
-            sb_y_row<TJ>(jobs, R.x, R.y, sh.ut, coef, sh.beff, sh.yt, lane);
+        if (R > 1 && st > 0) {   // multi-row warps over the stage's row groups
+            const int* gp = tb.gptr + ((R == 2 ? 0 : NST) + st) * 2;   // [begin, end) of the stage's groups
+            const int g0 = gp[0], g1 = gp[1];
+            for (;;) {
+                int g = 0;
+                if (lane == 0) g = atomicAdd(&sh.ctr[st], 1);
+                g = g0 + __shfl_sync(0xffffffffu, g, 0);
+                if (g >= g1) break;
+                sb_y_group<TJ>(tb, tb.groups[g], R, sh.ut, sh.beff, sh.yt, lane);
+            }
+        } else {
+            for (;;) {
+                int r = 0;
+                if (lane == 0) r = atomicAdd(&sh.ctr[st], 1);
+                r = r0 + __shfl_sync(0xffffffffu, r, 0);
+                if (r >= r1) break;
+                const int2 Rw = rows[r];
+                sb_y_row<TJ>(tb.jobs, Rw.x, Rw.y, sh.ut, tb.coef, sh.beff, sh.yt, lane);
+            }
         }
         __syncthreads();
     }
@@ -389,9 +529,7 @@ struct SBAtom {
 // All threads of the CTA call it with the same arguments.  at(slot) returns the SBAtom of the
 // batch's atom slot (slot < na).  Ends with a CTA barrier.
 template <int TJ, class AtomOf, class Side = SBNoSide>
-__device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, const int2* __restrict__ rows,
-                         const int* __restrict__ sptr, const float* __restrict__ coef,
-                         const SnapDevParams& sp, int na, const AtomOf& at, int n, const double box[3], int* status,
+__device__ void sb_batch(const SBShared<TJ>& sh, const SBTables& tb, const SnapDevParams& sp, int na, const AtomOf& at, int n, const double box[3], int* status,
                          bool want_forces, const Side& side = Side()) {
     constexpr int NH = Dims<TJ>::NHALF, NF = Dims<TJ>::NFULL;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -439,7 +577,7 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const int4* __restrict__ jobs, 
     __syncthreads();
     if (!want_forces) return;
 
-    sb_y_phase<TJ>(sh, jobs, rows, sptr, coef, lane, side);
+    sb_y_phase<TJ>(sh, tb, lane, na, side);
     sb_fill_middle<TJ>(sh.yt);
 
     // dE/dr phase

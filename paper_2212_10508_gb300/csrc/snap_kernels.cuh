@@ -20,6 +20,8 @@ struct SnapView {
     const int2* sbrows;      // job range of each (stage, row)
     const int* sbsptr;       // row ranges of the stages
     const float* sbcoef;     // per-job Clebsch-Gordan weights
+    const int2* sbgroups;    // row groups (first row, count) for multi-row warps
+    const int* sbgptr;       // [2][nstages][2] group ranges per stage (R = 2, 4)
     const double* beta;
     int ncg, nblk, nB;
     SnapDevParams sp;
@@ -126,6 +128,10 @@ __device__ inline void sb_shared_load(SBShared<TJ>& sh, const SnapView& v) {
         sh.ut[x - SB_GUARD * SB_LD] = make_float2(0.f, 0.f);
         sh.ut[(size_t)Dims<TJ>::NFULL * SB_LD + x] = make_float2(0.f, 0.f);
     }
+}
+
+inline __host__ __device__ SBTables sb_tables(const SnapView& v) {
+    return SBTables{v.sbjobs, v.sbrows, v.sbsptr, v.sbcoef, v.sbgroups, v.sbgptr};
 }
 
 // threads per CTA of the SNAP kernels: the batched FP32 design or one warp per atom (FP64)
