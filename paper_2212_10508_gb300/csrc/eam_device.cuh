@@ -5,7 +5,7 @@
 //   F'(rho) = -A / (2 sqrt rho), 0 when rho = 0.
 // Positions live in shared memory (FP64 rows plus a wrapped FP32 copy used to screen pairs).
 // FP64 mode evaluates every pair term in FP64 from the exact minimum-image displacement;
-// FP32_BULK evaluates pair terms and per-atom sums in FP32.
+// FP32_BULK evaluates pair terms, per-atom sums and the embedding derivative in FP32.
 #pragma once
 
 #include "device_common.cuh"
@@ -35,53 +35,61 @@ struct EamShared {
 constexpr int EAM_LIST_CAP = 64;
 constexpr float EAM_SKIN = 0.5f;
 
+// Position wrapped to [0, L) per axis (up to rounding) as FP32: x - L floor(x / L), with the
+// quotient taken as x * (1/L) (the reciprocals are loop invariants of every caller).
 __device__ __forceinline__ float4 wrap_f32(double x, double y, double z, const double box[3]) {
-    x -= box[0] * floor(x / box[0]);
-    y -= box[1] * floor(y / box[1]);
-    z -= box[2] * floor(z / box[2]);
+    const double i0 = 1.0 / box[0], i1 = 1.0 / box[1], i2 = 1.0 / box[2];
+    x -= box[0] * floor(x * i0);
+    y -= box[1] * floor(y * i1);
+    z -= box[2] * floor(z * i2);
     return make_float4((float)x, (float)y, (float)z, 0.f);
 }
 
-__device__ __forceinline__ bool screen_pair(const float4& a, const float4& b, const float boxf[3], float s2) {
+// FP32 minimum-image displacement b - a (ibf: reciprocal box lengths; the image only differs
+// from the one of a division for pairs near half a box length, far outside every cutoff).
+__device__ __forceinline__ float3 mi_f32(const float4& a, const float4& b, const float boxf[3], const float ibf[3]) {
     float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-    dx -= boxf[0] * rintf(dx / boxf[0]);
-    dy -= boxf[1] * rintf(dy / boxf[1]);
-    dz -= boxf[2] * rintf(dz / boxf[2]);
-    return dx * dx + dy * dy + dz * dz < s2;
+    dx -= boxf[0] * rintf(dx * ibf[0]);
+    dy -= boxf[1] * rintf(dy * ibf[1]);
+    dz -= boxf[2] * rintf(dz * ibf[2]);
+    return make_float3(dx, dy, dz);
 }
+__device__ __forceinline__ float r2_f32(const float3& d) { return d.x * d.x + d.y * d.y + d.z * d.z; }
 
-// exact pair geometry in the chosen precision: returns r and the displacement r_j - r_i
+// Pair (i, j) if within the screen radius: r and the displacement r_j - r_i in the chosen precision
+// (FP32: the screened FP32 displacement itself; FP64: the exact minimum image).  False otherwise.
 template <typename real>
-__device__ __forceinline__ real pair_geom(const EamShared& s, int n, int i, int j, const double box[3],
-                                          const float boxf[3], real d[3]) {
+__device__ __forceinline__ bool pair_in(const EamShared& s, int n, int i, int j, const float4& qi, const double box[3],
+                                        const float boxf[3], const float ibf[3], float screen2, real& r, real d[3]) {
+    if (j == i) return false;
+    const float3 df = mi_f32(qi, s.qf[j], boxf, ibf);
+    const float r2 = r2_f32(df);
+    if (!(r2 < screen2)) return false;
     if constexpr (sizeof(real) == 8) {
         double dd[3];
         disp64(s.q, n, i, j, box, dd);
         d[0] = dd[0];
         d[1] = dd[1];
         d[2] = dd[2];
-        return sqrt(r2_64(dd));
+        r = sqrt(r2_64(dd));
     } else {
-        const float4 a = s.qf[i], b = s.qf[j];
-        float dx = b.x - a.x, dy = b.y - a.y, dz = b.z - a.z;
-        dx -= boxf[0] * rintf(dx / boxf[0]);
-        dy -= boxf[1] * rintf(dy / boxf[1]);
-        dz -= boxf[2] * rintf(dz / boxf[2]);
-        d[0] = dx;
-        d[1] = dy;
-        d[2] = dz;
-        return sqrtf(dx * dx + dy * dy + dz * dz);
+        d[0] = df.x;
+        d[1] = df.y;
+        d[2] = df.z;
+        r = sqrtf(r2);
     }
+    return true;
 }
 
 __device__ __forceinline__ void eam_build_list(const EamShared& s, int n, const double box[3], float reach2,
                                                int* overflow) {
     const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
+    const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 qi = s.qf[i];
         int c = 0;
         for (int j = 0; j < n; ++j) {
-            if (j == i || !screen_pair(qi, s.qf[j], boxf, reach2)) continue;
+            if (j == i || !(r2_f32(mi_f32(qi, s.qf[j], boxf, ibf)) < reach2)) continue;
             if (c < EAM_LIST_CAP) s.nbl[i * EAM_LIST_CAP + c] = (unsigned short)j;
             ++c;
         }
@@ -110,6 +118,7 @@ __device__ __forceinline__ int eam_list_stale(const EamShared& s, int n) {
 template <typename real>
 __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], const FSDev& p, double* Eat) {
     const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
+    const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
     const real d_ = (real)p.d, c_ = (real)p.c, c0 = (real)p.c0, c1 = (real)p.c1, c2 = (real)p.c2;
     const bool list = s.nbl != nullptr;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -118,14 +127,16 @@ __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], c
         const int cnt = list ? s.nbc[i] : n;
         for (int t = 0; t < cnt; ++t) {
             const int j = list ? s.nbl[i * EAM_LIST_CAP + t] : t;
-            if (j == i || !screen_pair(qi, s.qf[j], boxf, p.screen2)) continue;
-            real dv[3];
-            const real r = pair_geom<real>(s, n, i, j, box, boxf, dv);
+            real dv[3], r;
+            if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
             if (r < d_) rho += (r - d_) * (r - d_);
             if (r < c_) ep += real(0.5) * ((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
         }
         const double rh = (double)rho;
-        s.dF[i] = rh > 0.0 ? -p.A / (2.0 * sqrt(rh)) : 0.0;
+        if constexpr (sizeof(real) == 4)   // FP32_BULK: the embedding derivative in FP32 as well
+            s.dF[i] = rho > 0.f ? (double)(-0.5f * (float)p.A / sqrtf(rho)) : 0.0;
+        else
+            s.dF[i] = rh > 0.0 ? -p.A / (2.0 * sqrt(rh)) : 0.0;
         if (Eat) Eat[i] = (double)ep - p.A * sqrt(rh);
     }
     __syncthreads();
@@ -136,9 +147,8 @@ __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], c
         const int cnt = list ? s.nbc[i] : n;
         for (int t = 0; t < cnt; ++t) {
             const int j = list ? s.nbl[i * EAM_LIST_CAP + t] : t;
-            if (j == i || !screen_pair(qi, s.qf[j], boxf, p.screen2)) continue;
-            real dv[3];
-            const real r = pair_geom<real>(s, n, i, j, box, boxf, dv);
+            real dv[3], r;
+            if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
             real dEdr = real(0);
             if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
             if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);

@@ -688,13 +688,13 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, do
                 b += p * p;
             }
             a += d2;
-            mx = fmax(mx, sqrt(d2));
+            mx = fmax(mx, d2);
         }
         if (metric == PMD_METRIC_REL) {
             num = sqrt(cta_sum(a, red));
             den = sqrt(cta_sum(b, red));
         } else {
-            num = cta_max(mx, red);
+            num = sqrt(cta_max(mx, red));   // max_i |dq_i| = sqrt(max_i |dq_i|^2)
         }
     }
     double delta = metric == PMD_METRIC_REL ? (den > 0 ? num / den : 0.0) : num;
@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, do
                 b += p * p;
             }
             a += d2;
-            mx = fmax(mx, sqrt(d2));
+            mx = fmax(mx, d2);
         }
         const int anybad = __syncthreads_or(bad ? 1 : 0);
         if (metric == PMD_METRIC_REL) {
@@ -752,7 +752,7 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, do
             den += sqrt(cta_sum(b, red));
             delta = num / den;
         } else {
-            num = fmax(num, cta_max(mx, red));
+            num = fmax(num, sqrt(cta_max(mx, red)));
             delta = num;
         }
         if (anybad || !isfinite(delta)) delta = INFINITY;

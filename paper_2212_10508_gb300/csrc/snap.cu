@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "pmd_internal.h"
+#include "eam_device.cuh"   // wrap_f32
 #include "snap_kernels.cuh"
 
 namespace pmd {
@@ -416,10 +417,8 @@ __global__ void k_wrap_f32(const double* __restrict__ pos, int nbatch, int n, do
     const long bb = idx / n, i = idx % n;
     const double* P = pos + bb * 3 * n;
     double x = P[i], y = P[n + i], z = P[2 * n + i];
-    x -= b0 * floor(x / b0);
-    y -= b1 * floor(y / b1);
-    z -= b2 * floor(z / b2);
-    qf[idx] = make_float4((float)x, (float)y, (float)z, 0.f);
+    const double box[3] = {b0, b1, b2};
+    qf[idx] = wrap_f32(x, y, z, box);
 }
 
 template <typename real, int TJ>

@@ -56,7 +56,7 @@ __device__ __forceinline__ void disp64(const double* q, int n, int i, int k, con
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         double x = __dsub_rn(q[a * n + k], q[a * n + i]);
-        double s = rint(x / box[a]);
+        double s = rint(x * (1.0 / box[a]));   // the image of x / box except near half a box length
         d[a] = __dsub_rn(x, __dmul_rn(box[a], s));
     }
 }
