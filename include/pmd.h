@@ -193,6 +193,32 @@ int pmd_sync_status(pmd_engine* e, pmd_stream_t stream);
  * receives the duration of the most recent such kernel (waits for it to finish), or -1 if none. */
 int pmd_engine_profile(pmd_engine* e, int enable, double* last_ms);
 
+/* Run-time shape of the batched FP32 fine kernel (the FP64 form ignores it):
+ *   rows2_atoms  batches of at most this many atoms (0..16) run the Y contraction with two output
+ *                rows per warp (half-warps of 16 atoms), rows4_atoms (0..8) with four rows per warp;
+ *   b_group      atoms per warp in the integrator phase (1..10);
+ *   noise_stage  Y stage (by sub-block size tb, 0 = tb <= 3) that also draws the Gaussian
+ *                increments of the batch, -1 = the stage of tb = 6.
+ * Results do not depend on the shape (every output keeps its arithmetic and order); only time
+ * does.  Defaults {16, 8, 8, -1}. */
+typedef struct {
+    int rows2_atoms, rows4_atoms, b_group, noise_stage;
+} pmd_fine_tuning;
+int pmd_engine_get_tuning(const pmd_engine* e, pmd_fine_tuning* out);
+int pmd_engine_set_tuning(pmd_engine* e, const pmd_fine_tuning* t);
+
+/* Autotuner of the batched FP32 fine kernel: times baoab_propagate_batch(PMD_FINE) on a copy of
+ * the given batch (q, v, member_stride, nsteps, interval_id, lp as in baoab_propagate_batch;
+ * the caller's arrays are not modified) with the interval lengths scaled down so that the
+ * longest takes max_steps steps (the shape of the active set over the sub-steps is kept), for a
+ * set of candidate shapes (coordinate search, two timed runs each), and keeps the fastest in the
+ * engine.  *chosen and *best_ms (each may be NULL) receive it and its time.  Setup call: it
+ * allocates device memory and synchronises the stream.  EUNSUPPORTED for an FP64 fine engine. */
+int pmd_engine_autotune(pmd_engine* e, int nbatch, int natoms, const double* q, const double* v,
+                        int64_t member_stride, const int32_t* nsteps, const int64_t* interval_id,
+                        const pmd_langevin* lp, int max_steps, pmd_stream_t stream, pmd_fine_tuning* chosen,
+                        double* best_ms);
+
 /* Propagate nbatch independent systems, member b for nsteps[b] steps of the Langevin scheme
  * lp driven by the fine (PMD_FINE, SNAP) or coarse (PMD_COARSE, EAM) potential, with noise
  * key n = interval_id[b]: member b computes F_dt or C_dt of the interval [n dt*L, ...]

@@ -59,6 +59,15 @@ class EngineParams(ctypes.Structure):
                 ("natoms", ctypes.c_int)]
 
 
+class FineTuning(ctypes.Structure):
+    """Run-time shape of the batched FP32 fine kernel (pmd_fine_tuning)."""
+    _fields_ = [("rows2_atoms", ctypes.c_int), ("rows4_atoms", ctypes.c_int), ("b_group", ctypes.c_int),
+                ("noise_stage", ctypes.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class Action(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("n_in", ctypes.c_int), ("n_fin", ctypes.c_int),
                 ("open_slab", ctypes.c_int), ("k", ctypes.c_int)]
@@ -68,6 +77,7 @@ EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_nu
            "pmd_snap_reserve",
            "snap_energy_forces", "pmd_snap_sync_status", "snap_energy_forces_noalloc", "eam_energy_forces", "pmd_engine_create",
            "pmd_engine_destroy", "pmd_engine_set_beta", "pmd_engine_reserve", "pmd_engine_profile", "pmd_sync_status",
+           "pmd_engine_get_tuning", "pmd_engine_set_tuning", "pmd_engine_autotune",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
            "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log"]
 
@@ -101,6 +111,10 @@ def lib():
     L.pmd_engine_reserve.argtypes = [vp, i32]
     L.pmd_engine_profile.argtypes = [vp, i32, dp]
     L.pmd_sync_status.argtypes = [vp, vp]
+    L.pmd_engine_get_tuning.argtypes = [vp, ctypes.POINTER(FineTuning)]
+    L.pmd_engine_set_tuning.argtypes = [vp, ctypes.POINTER(FineTuning)]
+    L.pmd_engine_autotune.argtypes = [vp, i32, i32, vp, vp, i64, vp, vp, ctypes.POINTER(Langevin), i32, vp,
+                                      ctypes.POINTER(FineTuning), dp]
     L.baoab_propagate_batch.argtypes = [vp, i32, i32, i32, vp, vp, i64, vp, vp, ctypes.POINTER(Langevin), vp]
     L.parareal_jumps.argtypes = [vp, i32, vp, vp, vp, vp]
     L.parareal_correct.argtypes = [vp, i32, i32, vp, vp, vp, vp, ctypes.c_double, i32, i32,
@@ -239,6 +253,32 @@ class Engine:
         ms = ctypes.c_double()
         _check(lib().pmd_engine_profile(self.h, 1 if enable else 0, ctypes.byref(ms)))
         return ms.value
+
+    def tuning(self):
+        """The engine's run-time shape of the batched FP32 fine kernel, as a dict."""
+        t = FineTuning()
+        _check(lib().pmd_engine_get_tuning(self.h, ctypes.byref(t)))
+        return t.as_dict()
+
+    def set_tuning(self, **kw):
+        t = FineTuning(**{**self.tuning(), **kw})
+        _check(lib().pmd_engine_set_tuning(self.h, ctypes.byref(t)))
+
+    def autotune(self, q, v, nsteps, interval_id, lp: Langevin, max_steps=64, stream=None):
+        """Time candidate shapes on a copy of this batch (lengths scaled to at most max_steps) and
+        keep the fastest; returns (shape dict, best ms).  q, v as in baoab_propagate_batch."""
+        nb = q.shape[0]
+        if v is None:
+            qp = _ptr(q)
+            vp = ctypes.c_void_p(qp.value + 3 * self.natoms * 8)
+            stride = 6 * self.natoms
+        else:
+            qp, vp, stride = _ptr(q), _ptr(v), 3 * self.natoms
+        t, ms = FineTuning(), ctypes.c_double()
+        _check(lib().pmd_engine_autotune(self.h, nb, self.natoms, qp, vp, stride, _ptr(nsteps), _ptr(interval_id),
+                                         ctypes.byref(lp), int(max_steps), _stream(stream), ctypes.byref(t),
+                                         ctypes.byref(ms)))
+        return t.as_dict(), ms.value
 
     def baoab_propagate_batch(self, potential, q, v, nsteps, interval_id, lp: Langevin, stream=None):
         """Propagate members in place.  q, v: [nb,3,n]; or v=None and q packed states [nb,6,n]

@@ -106,6 +106,8 @@ static int check_langevin(const pmd_langevin* lp) {
     return PMD_OK;
 }
 
+int check_langevin_params(const pmd_langevin* lp) { return check_langevin(lp); }
+
 static int read_status(int* dstatus, cudaStream_t st) {
     int h = 0;
     PMD_CUDA_TRY(cudaMemcpyAsync(&h, dstatus, sizeof(int), cudaMemcpyDeviceToHost, st));

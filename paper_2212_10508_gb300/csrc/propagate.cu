@@ -73,6 +73,8 @@ struct FineArgs {
     int* status;
     double* gstep;          // FP32 path: G_{ell} of the sub-step's items [item][3], drawn in phase A
     unsigned char* pos;     // reverse-slot tables [member][n][n], or nullptr (binary search)
+    SBShape shape;          // FP32 path: run-time shape of the batched pass
+    int b_group;            // atoms per warp in phase B (1..SB_B_GROUP_MAX)
 };
 
 __global__ void k_fine_prologue(const int32_t* __restrict__ nsteps, int nbatch, int schedule, int* __restrict__ order,
@@ -123,16 +125,17 @@ __device__ __forceinline__ int active_members(const int* Ls, int nbatch, int ell
     return lo;
 }
 
-// Phase B of sub-step ell for the items it = first + r * stride, r < SB_B_GROUP, it < items, one
+// Phase B of sub-step ell for the items it = first + r * stride, r < group, it < items, one
 // warp: the noise G_{ell,n} of all the group's atoms (FP32 path: drawn during phase A and read
 // from gstep; FP64 path: lanes 2r and 2r+1 draw Philox blocks 0 and 1 of atom r: G_x, G_y and
 // G_z), the force gather of each atom (whole warp, lanes = neighbour slots), and the Langevin
 // update of all atoms at once (lane 3r + al advances component al of atom r).  Positions and
 // velocities are loaded before the gathers.
-constexpr int SB_B_GROUP = 8;
+constexpr int SB_B_GROUP_MAX = 10;   // 3 lanes per atom for the update
 
 template <typename real>
 __device__ __noinline__ void fine_phase_b(const FineArgs& a, long first, long stride, long items, int ell, int lane) {
+    const int SB_B_GROUP = a.b_group;
     const int n = a.n;
     const LangevinDev& Lp = a.L;
     const double box[3] = {a.box0, a.box1, a.box2};
@@ -280,7 +283,7 @@ __device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, lo
                               a.pos ? a.pos + ((size_t)m * n + i) * n : nullptr};
             };
             const FineNoiseSide side{&a, bs, na, ell};
-            sb_batch<TJ>(sh, sb_tables(a.v), a.v.sp, na, at, n, box, a.status, true, side);
+            sb_batch<TJ>(sh, sb_tables(a.v), a.v.sp, na, at, n, box, a.status, true, side, a.shape);
         }
     } else {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -311,7 +314,7 @@ __device__ __forceinline__ void fine_loop(const FineArgs& a, const SH& sh) {
         const long items = (long)A * n;
         fine_phase_a<real, TJ>(a, sh, items, box, ell);
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
-        for (long first = gwarp; first < items; first += (long)SB_B_GROUP * nwarps)
+        for (long first = gwarp; first < items; first += (long)a.b_group * nwarps)
             fine_phase_b<real>(a, first, nwarps, items, ell, lane);
         if (!grid_sync(gb, a.status, ST_TIMEOUT)) return;
     }
@@ -356,6 +359,10 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
     a.qf = e->s_qf.as<float4>();
     a.vh = e->s_vh.as<double>();
     a.gstep = e->s_gstep.as<double>();
+    a.shape.rows2_atoms = e->tune.rows2_atoms;
+    a.shape.rows4_atoms = e->tune.rows4_atoms;
+    a.shape.noise_stage = e->tune.noise_stage;
+    a.b_group = e->tune.b_group < 1 ? 1 : (e->tune.b_group > SB_B_GROUP_MAX ? SB_B_GROUP_MAX : e->tune.b_group);
     a.pos = n <= PMD_POS_TABLE_MAX_ATOMS && sizeof(real) == 4 ? e->s_pos.as<unsigned char>() : nullptr;
     a.order = e->s_order.as<int>();
     a.Ls = e->s_order.as<int>() + e->cap_batch;

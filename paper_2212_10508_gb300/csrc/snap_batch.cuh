@@ -74,6 +74,13 @@ struct SBNoSide {
     __device__ void operator()(int, int) const {}
 };
 
+// Run-time shape of the batched pass (chosen by pmd_engine_autotune; defaults below).
+struct SBShape {
+    int rows2_atoms = 16;   // batches of at most this many atoms (<= 16) run the Y phase 2 rows per warp
+    int rows4_atoms = 8;    // ... and of at most this many atoms (<= 8) 4 rows per warp
+    int noise_stage = -1;   // Y stage that also draws the Gaussian increments (-1: the stage of b = 6)
+};
+
 // Device tables of the batched Y contraction.
 struct SBTables {
     const int4* jobs;     // job records
@@ -383,13 +390,14 @@ __device__ __noinline__ void sb_y_row(const int4* __restrict__ jobs, int j0, int
 // The whole Y phase of a batch (all threads of the CTA; ends with a CTA barrier).
 template <int TJ, class Side = SBNoSide>
 __device__ __forceinline__ void sb_y_phase(const SBShared<TJ>& sh, const SBTables& tb, int lane, int na = SB_ATOMS,
-                                           const Side& side = Side()) {
-    constexpr int side_stage = sb_stage_of(TJ >= 6 ? 6 : TJ);
+                                           const Side& side = Side(), const SBShape& shape = SBShape()) {
+    const int side_stage = shape.noise_stage >= 0 && shape.noise_stage < sb_num_stages(TJ)
+                               ? shape.noise_stage : sb_stage_of(TJ >= 6 ? 6 : TJ);
     constexpr int NST = sb_num_stages(TJ);
     const int2* __restrict__ rows = tb.rows;
     const int* __restrict__ sptr = tb.sptr;
     // rows per warp pass: 4 sub-warps of 8 lanes for <= 8 atoms, 2 of 16 for <= 16 (stages b >= 4)
-    const int R = na <= 8 ? 4 : (na <= 16 ? 2 : 1);
+    const int R = na <= shape.rows4_atoms && na <= 8 ? 4 : (na <= shape.rows2_atoms && na <= 16 ? 2 : 1);
     for (int x = threadIdx.x; x < Dims<TJ>::NHALF * SB_LD; x += blockDim.x) sh.yt[x] = make_float2(0.f, 0.f);
     if (threadIdx.x < SB_MAX_STAGES) sh.ctr[threadIdx.x] = 0;
     __syncthreads();
@@ -530,7 +538,7 @@ struct SBAtom {
 // batch's atom slot (slot < na).  Ends with a CTA barrier.
 template <int TJ, class AtomOf, class Side = SBNoSide>
 __device__ void sb_batch(const SBShared<TJ>& sh, const SBTables& tb, const SnapDevParams& sp, int na, const AtomOf& at, int n, const double box[3], int* status,
-                         bool want_forces, const Side& side = Side()) {
+                         bool want_forces, const Side& side = Side(), const SBShape& shape = SBShape()) {
     constexpr int NH = Dims<TJ>::NHALF, NF = Dims<TJ>::NFULL;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float kappa = float(sp.rfac0 * PI / sp.rcut);
@@ -577,7 +585,7 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const SBTables& tb, const SnapD
     __syncthreads();
     if (!want_forces) return;
 
-    sb_y_phase<TJ>(sh, tb, lane, na, side);
+    sb_y_phase<TJ>(sh, tb, lane, na, side, shape);
     sb_fill_middle<TJ>(sh.yt);
 
     // dE/dr phase

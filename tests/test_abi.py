@@ -54,6 +54,10 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.eam_energy_forces(ctypes.byref(fs), 1, 10, small, None, None, None, None) == P.PMD_EINVAL
     assert lib.pmd_adaptive_create(10, 0.5, 0.1, ctypes.byref(h)) == P.PMD_EINVAL
     assert lib.adaptive_restart(None, 0.0, 0, None) == P.PMD_EINVAL
+    t = P.FineTuning(16, 8, 8, -1)
+    assert lib.pmd_engine_set_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
+    assert lib.pmd_engine_get_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
+    assert lib.pmd_engine_autotune(None, 1, 1, None, None, 3, None, None, None, 1, None, None, None) == P.PMD_EINVAL
 
 
 def _replay(N, dc, de, trace):
