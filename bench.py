@@ -152,9 +152,11 @@ def _avg_neighbors(q, box, rc):
     return tot / (q.shape[0] * q.shape[2])
 
 
-def _cpu_baseline(q, v, box, beta, L, ids, budget_s=12.0):
+def _cpu_baseline(q, v, box, beta, L, ids, budget_s=12.0, compare=None):
     """The oracle as it stands on the host cores: first members of the batch, first 20 steps each,
-    growing the sample until it has run for about budget_s."""
+    growing the sample until it has run for about budget_s.  compare(q0, v0, Ls, ids, q1, v1, O), if
+    given, receives the sample's inputs and the oracle's final states and returns the GPU results'
+    errors against the oracle (reported with the baseline)."""
     import oracle as O
     pot = O.potential(O.POT_SNAP, beta=beta)
     lp = O.langevin(dt=DT, gamma=GAMMA, T=TEMP, seed=2212, schedule=O.SCHED_ROBUST)
@@ -167,9 +169,12 @@ def _cpu_baseline(q, v, box, beta, L, ids, budget_s=12.0):
         dt = time.perf_counter() - t0
         if dt >= budget_s / 3 or nm >= q.shape[0]:
             atom_steps = float(Ls.sum()) * q.shape[2]
-            return {"value": atom_steps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                    "sample": "%d of the 64 intervals x %d steps each (129 atoms, FP64 oracle, %.1f s)"
-                              % (nm, steps, dt)}
+            res = {"value": atom_steps / dt, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                   "sample": "%d of the 64 intervals x %d steps each (129 atoms, FP64 oracle, %.1f s)"
+                             % (nm, steps, dt)}
+            if compare is not None:
+                res["errors_vs_oracle"] = compare(q[:nm], v[:nm], Ls, ids[:nm], qq, vv, O)
+            return res
         nm = min(q.shape[0], nm * 2)
 
 
@@ -434,7 +439,28 @@ def run_ours(args):
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
     if rank == 0 and ws == 1 and not args.no_cpu:
-        out["cpu_baseline"] = _cpu_baseline(q, v, box, beta, L, ids)
+        def compare(q0, v0, Ls, sids, q1, v1, O):
+            """GPU FP32-bulk and FP64 results on the oracle's sample: trajectory (max |dq| in A after the
+            sample's steps) and, on member 0's start configuration, energy and force relative errors."""
+            err = {}
+            dq0 = torch.as_tensor(q0, device=dev)
+            dv0 = torch.as_tensor(v0, device=dev)
+            dL = torch.as_tensor(Ls, device=dev)
+            dids = torch.as_tensor(sids, device=dev)
+            E_o, F_o, _ = O.snap_energy_forces(q0[:1], box, beta)
+            for name, prec in (("fp32_bulk", P.FP32_BULK), ("fp64", P.FP64)):
+                e = P.Engine(n, box, P.snap_params(precision=prec), P.fs_params(), beta=tbeta)
+                qq, vv = dq0.clone(), dv0.clone()
+                e.baoab_propagate_batch(P.FINE, qq, vv, dL, dids, lp)
+                e.sync_status()
+                err[name + "_traj_max_dq_A"] = float(np.abs(qq.cpu().numpy() - q1).max())
+                err[name + "_traj_max_dv_rel"] = float(np.abs(vv.cpu().numpy() - v1).max() / np.abs(v1).max())
+                E_g, F_g, _ = P.snap_energy_forces(P.Snap(P.snap_params(precision=prec)), dq0[:1], box, tbeta)
+                err[name + "_energy_rel"] = float(abs(E_g.cpu().numpy()[0] - E_o[0]) / abs(E_o[0]))
+                err[name + "_force_rel_max"] = float(np.abs(F_g.cpu().numpy() - F_o).max() / np.abs(F_o).max())
+            err["steps"] = int(Ls.max())
+            return err
+        out["cpu_baseline"] = _cpu_baseline(q, v, box, beta, L, ids, compare=compare)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
