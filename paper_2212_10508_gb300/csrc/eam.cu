@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(512) k_eam_standalone(int n, double b0, double
 
 int eam_launch(const pmd_fs_params& p, int nbatch, int n, const double box[3], const double* pos, double* energy,
                double* forces, cudaStream_t st) {
-    const int threads = std::min(512, (n + 31) / 32 * 32);
+    // the launch shape of the coarse propagation kernels: two threads per atom up to 256 atoms
+    const int threads = std::min(512, ((2 * n <= 512 ? 2 * n : n) + 31) / 32 * 32);
     const size_t sm = (size_t)n * (3 * 8 + 3 * 8 + 8 + 8 + 16) + 64;
     const FSDev fs = make_fs(p);
     auto go = [&](auto kern) -> int {

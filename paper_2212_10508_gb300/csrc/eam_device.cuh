@@ -111,9 +111,9 @@ __device__ __forceinline__ int eam_list_stale(const EamShared& s, int n) {
     return __syncthreads_or(stale);
 }
 
-// Forces into s.F (and per-atom energies into Eat if non-null).  All threads of the CTA call
-// it; it ends with __syncthreads().  With a list (s.nbl != nullptr) the caller keeps it valid
-// (eam_refresh_list); otherwise every atom is scanned.  FP64 accumulates in double, FP32_BULK in
+// Forces into s.F (and per-atom energies into Eat if non-null).  All threads of the CTA call it
+// (blockDim a multiple of 32); it ends with __syncthreads().  With a list (s.nbl != nullptr) the
+// caller keeps it valid (eam_refresh_list); otherwise every atom is scanned.  FP64 accumulates in double, FP32_BULK in
 // float (pair terms and sums).
 template <typename real>
 __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], const FSDev& p, double* Eat) {
@@ -121,46 +121,74 @@ __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], c
     const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
     const real d_ = (real)p.d, c_ = (real)p.c, c0 = (real)p.c0, c1 = (real)p.c1, c2 = (real)p.c2;
     const bool list = s.nbl != nullptr;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float4 qi = s.qf[i];
+    // S threads per atom when the CTA has at least 2n threads (the launch shape decides; every
+    // coarse kernel uses the same one): thread u of atom i sums its pair entries u, u + S, ...,
+    // and the two partial sums are combined by an xor-shuffle (symmetric: both threads hold the
+    // same bits).  span covers whole warps so that every lane takes part in the shuffles.
+    const int S = (int)blockDim.x >= 2 * n ? 2 : 1;
+    const int span = (S * n + 31) / 32 * 32;
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        const int i = t / S, u = t - (t / S) * S;
+        const bool act = i < n;
         real rho = 0, ep = 0;
-        const int cnt = list ? s.nbc[i] : n;
-        for (int t = 0; t < cnt; ++t) {
-            const int j = list ? s.nbl[i * EAM_LIST_CAP + t] : t;
-            real dv[3], r;
-            if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
-            if (r < d_) rho += (r - d_) * (r - d_);
-            if (r < c_) ep += real(0.5) * ((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
-        }
-        const double rh = (double)rho;
-        if constexpr (sizeof(real) == 4)   // FP32_BULK: the embedding derivative in FP32 as well
-            s.dF[i] = rho > 0.f ? (double)(-0.5f * (float)p.A / sqrtf(rho)) : 0.0;
-        else
-            s.dF[i] = rh > 0.0 ? -p.A / (2.0 * sqrt(rh)) : 0.0;
-        if (Eat) Eat[i] = (double)ep - p.A * sqrt(rh);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float4 qi = s.qf[i];
-        const real dFi = (real)s.dF[i];
-        real f0 = 0, f1 = 0, f2 = 0;
-        const int cnt = list ? s.nbc[i] : n;
-        for (int t = 0; t < cnt; ++t) {
-            const int j = list ? s.nbl[i * EAM_LIST_CAP + t] : t;
-            real dv[3], r;
-            if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
-            real dEdr = real(0);
-            if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
-            if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
-            if (r < d_ || r < c_) {
-                f0 += dEdr * dv[0] / r;
-                f1 += dEdr * dv[1] / r;
-                f2 += dEdr * dv[2] / r;
+        if (act) {
+            const float4 qi = s.qf[i];
+            const int cnt = list ? s.nbc[i] : n;
+            for (int c = u; c < cnt; c += S) {
+                const int j = list ? s.nbl[i * EAM_LIST_CAP + c] : c;
+                real dv[3], r;
+                if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
+                if (r < d_) rho += (r - d_) * (r - d_);
+                if (r < c_) ep += real(0.5) * ((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
             }
         }
-        s.F[i] = (double)f0;
-        s.F[n + i] = (double)f1;
-        s.F[2 * n + i] = (double)f2;
+        if (S == 2) {
+            rho += __shfl_xor_sync(0xffffffffu, rho, 1);
+            ep += __shfl_xor_sync(0xffffffffu, ep, 1);
+        }
+        if (act && u == 0) {
+            const double rh = (double)rho;
+            if constexpr (sizeof(real) == 4)   // FP32_BULK: the embedding derivative in FP32 as well
+                s.dF[i] = rho > 0.f ? (double)(-0.5f * (float)p.A / sqrtf(rho)) : 0.0;
+            else
+                s.dF[i] = rh > 0.0 ? -p.A / (2.0 * sqrt(rh)) : 0.0;
+            if (Eat) Eat[i] = (double)ep - p.A * sqrt(rh);
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < span; t += blockDim.x) {
+        const int i = t / S, u = t - (t / S) * S;
+        const bool act = i < n;
+        real f0 = 0, f1 = 0, f2 = 0;
+        if (act) {
+            const float4 qi = s.qf[i];
+            const real dFi = (real)s.dF[i];
+            const int cnt = list ? s.nbc[i] : n;
+            for (int c = u; c < cnt; c += S) {
+                const int j = list ? s.nbl[i * EAM_LIST_CAP + c] : c;
+                real dv[3], r;
+                if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
+                real dEdr = real(0);
+                if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
+                if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
+                if (r < d_ || r < c_) {
+                    const real g = dEdr / r;
+                    f0 += g * dv[0];
+                    f1 += g * dv[1];
+                    f2 += g * dv[2];
+                }
+            }
+        }
+        if (S == 2) {
+            f0 += __shfl_xor_sync(0xffffffffu, f0, 1);
+            f1 += __shfl_xor_sync(0xffffffffu, f1, 1);
+            f2 += __shfl_xor_sync(0xffffffffu, f2, 1);
+        }
+        if (act && u == 0) {
+            s.F[i] = (double)f0;
+            s.F[n + i] = (double)f1;
+            s.F[2 * n + i] = (double)f2;
+        }
     }
     __syncthreads();
 }

@@ -607,8 +607,10 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_coarse_batch(int n, doub
     store_state<KMAX>(s, own, n, q + m * stride, v + m * stride);
 }
 
+// Threads of the one-CTA coarse kernels (batch and sweep use the same shape, so their force sums
+// are bit for bit the same): two threads per atom in the pair loops up to 256 atoms, one beyond.
 static void coarse_shape(int n, int& threads, int& kmax) {
-    threads = std::min(COARSE_MAX_THREADS, (n + 31) / 32 * 32);
+    threads = std::min(COARSE_MAX_THREADS, ((2 * n <= COARSE_MAX_THREADS ? 2 * n : n) + 31) / 32 * 32);
     kmax = (n + threads - 1) / threads;
 }
 
