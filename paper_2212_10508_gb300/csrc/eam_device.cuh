@@ -99,15 +99,16 @@ __device__ __forceinline__ void eam_build_list(const EamShared& s, int n, const 
     }
 }
 
-// 1 when some atom moved more than half the skin since the list was built (CTA-uniform)
-__device__ __forceinline__ int eam_list_stale(const EamShared& s, int n) {
+// 1 when some atom moved more than half the skin since the list was built (CTA-uniform); the
+// displacement is taken with the minimum image, so that crossing a face of the box (a jump of
+// the wrapped position by a box length) is not a move
+__device__ __forceinline__ int eam_list_stale(const EamShared& s, int n, const double box[3]) {
     int stale = 0;
     const float lim2 = 0.25f * EAM_SKIN * EAM_SKIN;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const float4 a = s.qf[i], b = s.qref[i];
-        const float dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
-        if (dx * dx + dy * dy + dz * dz > lim2) stale = 1;
-    }
+    const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
+    const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (r2_f32(mi_f32(s.qref[i], s.qf[i], boxf, ibf)) > lim2) stale = 1;
     return __syncthreads_or(stale);
 }
 
@@ -197,7 +198,7 @@ __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], c
 __device__ __forceinline__ void eam_refresh_list(const EamShared& s, int n, const double box[3], const FSDev& p,
                                                  bool force_build, int* status) {
     if (!s.nbl) return;
-    const int stale = force_build ? 1 : eam_list_stale(s, n);
+    const int stale = force_build ? 1 : eam_list_stale(s, n, box);
     if (stale) {
         __shared__ int overflow;
         if (threadIdx.x == 0) overflow = 0;
