@@ -22,6 +22,9 @@ __global__ void __launch_bounds__(512) k_eam_standalone(int n, double b0, double
     s.nbl = nullptr;   // one evaluation: scan all atoms
     s.nbc = nullptr;
     s.qref = nullptr;
+    s.pg = nullptr;
+    s.pj = nullptr;
+    s.pgc = nullptr;
     const double box[3] = {b0, b1, b2};
     const long m = blockIdx.x;
     const double* P = pos + m * 3 * n;

@@ -23,9 +23,13 @@ struct EamShared {
     float4* qf;                // [n] wrapped to [0, L)
     double* F;                 // [3][n]
     double* dF;                // [n]
-    unsigned short* nbl;       // [n][EAM_LIST_CAP] Verlet list (nullptr: scan all atoms)
+    unsigned short* nbl;       // Verlet list, EAM_LIST_CAP per atom, eam_pidx layout (nullptr: scan all atoms)
     unsigned char* nbc;        // [n] list lengths
     float4* qref;              // [n] wrapped positions at the last list build
+    float4* pg;                // FP32 pair geometry (dx, dy, dz, r) of the density pass, EAM_PG_CAP per atom,
+                               // eam_pidx layout
+    unsigned short* pj;        // its neighbour indices (nullptr: no cache)
+    unsigned char* pgc;        // [n][2] entries per thread slot, EAM_PG_FULL when a slot overflowed
 };
 
 // Verlet list of the one-CTA coarse path: every pair within max(d, c) + EAM_SKIN, in index
@@ -34,6 +38,25 @@ struct EamShared {
 // a scan over all atoms (bitwise the same sums).
 constexpr int EAM_LIST_CAP = 64;
 constexpr float EAM_SKIN = 0.5f;
+
+// FP32 pairs within the screen radius kept from the density pass for the force pass: up to
+// EAM_PG_CAP per atom (EAM_PG_CAP / S per thread, k-th pair of thread u of atom i in slot
+// eam_pidx(i, u + k S, n, S)); a thread whose pairs do not fit recomputes them in the force pass,
+// with the same arithmetic.
+constexpr int EAM_PG_CAP = 24;
+constexpr unsigned char EAM_PG_FULL = 255;
+
+// Threads per atom in the pair passes of a CTA of blockDim.x threads: two when there are at least
+// 2n threads (thread u of atom i takes the pair entries u, u + 2, ...), one otherwise.
+__device__ __forceinline__ int eam_split(int n) { return (int)blockDim.x >= 2 * n ? 2 : 1; }
+
+// Slot of pair entry c of atom i in the list and the pair cache: [c / S][i][c % S], so that the
+// threads of consecutive atoms, which walk their entries in step, read consecutive elements
+// (no shared-memory bank conflicts).
+__device__ __forceinline__ int eam_pidx(int i, int c, int n, int S) {
+    const int k = S == 2 ? c >> 1 : c;
+    return k * (S * n) + i * S + (c - k * S);
+}
 
 // Position wrapped to [0, L) per axis (up to rounding) as FP32: x - L floor(x / L), with the
 // quotient taken as x * (1/L) (the reciprocals are loop invariants of every caller).
@@ -85,12 +108,13 @@ __device__ __forceinline__ void eam_build_list(const EamShared& s, int n, const 
                                                int* overflow) {
     const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
     const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
+    const int S = eam_split(n);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 qi = s.qf[i];
         int c = 0;
         for (int j = 0; j < n; ++j) {
             if (j == i || !(r2_f32(mi_f32(qi, s.qf[j], boxf, ibf)) < reach2)) continue;
-            if (c < EAM_LIST_CAP) s.nbl[i * EAM_LIST_CAP + c] = (unsigned short)j;
+            if (c < EAM_LIST_CAP) s.nbl[eam_pidx(i, c, n, S)] = (unsigned short)j;
             ++c;
         }
         if (c > EAM_LIST_CAP) atomicOr(overflow, 1);
@@ -112,21 +136,39 @@ __device__ __forceinline__ int eam_list_stale(const EamShared& s, int n, const d
     return __syncthreads_or(stale);
 }
 
+// Force term of pair (i, j) at distance r, displacement dv = r_j - r_i, added to f
+template <typename real>
+__device__ __forceinline__ void eam_pair_force(const EamShared& s, int j, real r, const real dv[3], real dFi, real d_,
+                                               real c_, real c0, real c1, real c2, real& f0, real& f1, real& f2) {
+    real dEdr = real(0);
+    if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
+    if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
+    if (r < d_ || r < c_) {
+        const real g = dEdr / r;
+        f0 += g * dv[0];
+        f1 += g * dv[1];
+        f2 += g * dv[2];
+    }
+}
+
 // Forces into s.F (and per-atom energies into Eat if non-null).  All threads of the CTA call it
 // (blockDim a multiple of 32); it ends with __syncthreads().  With a list (s.nbl != nullptr) the
-// caller keeps it valid (eam_refresh_list); otherwise every atom is scanned.  FP64 accumulates in double, FP32_BULK in
-// float (pair terms and sums).
-template <typename real>
-__device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], const FSDev& p, double* Eat) {
+// caller keeps it valid (eam_refresh_list); otherwise every atom is scanned.  FP64 accumulates in
+// double, FP32_BULK in float (pair terms and sums).  PGCACHE compiles in the pair-geometry cache
+// (used when the shared layout has one, FP32 only): the force pass then reads the pairs of the
+// density pass instead of screening the list again, with the same bits.
+template <typename real, bool PGCACHE = false>
+__device__ __forceinline__ void eam_forces_cta(const EamShared& s, int n, const double box[3], const FSDev& p, double* Eat) {
     const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
     const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
     const real d_ = (real)p.d, c_ = (real)p.c, c0 = (real)p.c0, c1 = (real)p.c1, c2 = (real)p.c2;
     const bool list = s.nbl != nullptr;
+    const bool cache = PGCACHE && sizeof(real) == 4 && s.pj != nullptr;
     // S threads per atom when the CTA has at least 2n threads (the launch shape decides; every
     // coarse kernel uses the same one): thread u of atom i sums its pair entries u, u + S, ...,
     // and the two partial sums are combined by an xor-shuffle (symmetric: both threads hold the
     // same bits).  span covers whole warps so that every lane takes part in the shuffles.
-    const int S = (int)blockDim.x >= 2 * n ? 2 : 1;
+    const int S = eam_split(n);
     const int span = (S * n + 31) / 32 * 32;
     for (int t = threadIdx.x; t < span; t += blockDim.x) {
         const int i = t / S, u = t - (t / S) * S;
@@ -135,13 +177,23 @@ __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], c
         if (act) {
             const float4 qi = s.qf[i];
             const int cnt = list ? s.nbc[i] : n;
-            for (int c = u; c < cnt; c += S) {
-                const int j = list ? s.nbl[i * EAM_LIST_CAP + c] : c;
+            const int cap = EAM_PG_CAP / S, stride = S * n;
+            int np = 0;
+            for (int c = u, o = i * S + u; c < cnt; c += S, o += stride) {   // o = eam_pidx(i, c, n, S)
+                const int j = list ? s.nbl[o] : c;
                 real dv[3], r;
                 if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
+                if constexpr (sizeof(real) == 4) {
+                    if (cache && np < cap) {
+                        s.pg[np * stride + i * S + u] = make_float4(dv[0], dv[1], dv[2], r);
+                        s.pj[np * stride + i * S + u] = (unsigned short)j;
+                    }
+                    ++np;
+                }
                 if (r < d_) rho += (r - d_) * (r - d_);
                 if (r < c_) ep += real(0.5) * ((r - c_) * (r - c_) * (c0 + c1 * r + c2 * r * r));
             }
+            if (cache) s.pgc[2 * i + u] = np > cap ? EAM_PG_FULL : (unsigned char)np;
         }
         if (S == 2) {
             rho += __shfl_xor_sync(0xffffffffu, rho, 1);
@@ -162,21 +214,24 @@ __device__ void eam_forces_cta(const EamShared& s, int n, const double box[3], c
         const bool act = i < n;
         real f0 = 0, f1 = 0, f2 = 0;
         if (act) {
-            const float4 qi = s.qf[i];
             const real dFi = (real)s.dF[i];
-            const int cnt = list ? s.nbc[i] : n;
-            for (int c = u; c < cnt; c += S) {
-                const int j = list ? s.nbl[i * EAM_LIST_CAP + c] : c;
-                real dv[3], r;
-                if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
-                real dEdr = real(0);
-                if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
-                if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
-                if (r < d_ || r < c_) {
-                    const real g = dEdr / r;
-                    f0 += g * dv[0];
-                    f1 += g * dv[1];
-                    f2 += g * dv[2];
+            const int np = cache ? s.pgc[2 * i + u] : EAM_PG_FULL;
+            const int stride = S * n;
+            if (np != EAM_PG_FULL) {   // the pairs of the density pass, in the same order
+#pragma unroll 1
+                for (int k = 0, o = i * S + u; k < np; ++k, o += stride) {
+                    const float4 g = s.pg[o];
+                    const real dv[3] = {(real)g.x, (real)g.y, (real)g.z};
+                    eam_pair_force<real>(s, s.pj[o], (real)g.w, dv, dFi, d_, c_, c0, c1, c2, f0, f1, f2);
+                }
+            } else {
+                const float4 qi = s.qf[i];
+                const int cnt = list ? s.nbc[i] : n;
+                for (int c = u, o = i * S + u; c < cnt; c += S, o += stride) {
+                    const int j = list ? s.nbl[o] : c;
+                    real dv[3], r;
+                    if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
+                    eam_pair_force<real>(s, j, r, dv, dFi, d_, c_, c0, c1, c2, f0, f1, f2);
                 }
             }
         }

@@ -22,7 +22,7 @@ namespace pmd {
 SnapView snap_view(const pmd_snap* s, const double* beta);
 int snap_reserve_impl(pmd_snap* s, long na);
 
-constexpr int COARSE_MAX_THREADS = 512;   // 90 registers per thread: 512 fit the register file
+constexpr int COARSE_MAX_THREADS = 512;   // one CTA per SM, up to 128 registers per thread
 
 // ---- host-side parameter packing -----------------------------------------------------------
 LangevinDev make_langevin(const pmd_langevin& lp) {
@@ -432,10 +432,12 @@ struct OwnState {
 };
 
 constexpr int EAM_LIST_MAX_ATOMS = 512;   // systems up to this size keep a Verlet list in shared memory
+constexpr int EAM_PG_MAX_ATOMS = 256;     // ... and up to this size the FP32 pair-geometry cache
 
 __host__ __device__ inline size_t coarse_smem_bytes(int n) {
     size_t b = (size_t)n * (3 * 8 + 16 + 3 * 8 + 8) + 64;
     if (n <= EAM_LIST_MAX_ATOMS) b += (size_t)n * (EAM_LIST_CAP * 2 + 1 + 16) + 64;
+    if (n <= EAM_PG_MAX_ATOMS) b += (size_t)n * (EAM_PG_CAP * (16 + 2) + 2) + 64;
     return b;
 }
 
@@ -453,6 +455,14 @@ __device__ inline EamShared coarse_carve(unsigned char* smem, int n) {
         s.qref = nullptr;
         s.nbl = nullptr;
         s.nbc = nullptr;
+    }
+    s.pg = nullptr;
+    s.pj = nullptr;
+    s.pgc = nullptr;
+    if (n <= EAM_PG_MAX_ATOMS) {
+        s.pg = reinterpret_cast<float4*>(align_up(reinterpret_cast<size_t>(s.nbc + n), 16));
+        s.pj = reinterpret_cast<unsigned short*>(s.pg + (size_t)n * EAM_PG_CAP);
+        s.pgc = reinterpret_cast<unsigned char*>(s.pj + (size_t)n * EAM_PG_CAP);
     }
     return s;
 }
@@ -477,19 +487,22 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                                     const FSDev& fs, const LangevinDev& L, int nsteps, int64_t nid, const double* Gpre,
                                     bool& list_ok, int* status) {
     if (nsteps <= 0) return;
+    // the Gaussian increments are loaded before the force evaluation that precedes their use
+    double Gc[KMAX][3];
+#pragma unroll
+    for (int k = 0; k < KMAX; ++k) {
+        const int i = threadIdx.x + k * blockDim.x;
+        if (i < n) coarse_noise<KMAX>(L, Gpre, nid, 0, i, n, Gc[k]);
+    }
     eam_refresh_list(s, n, box, fs, !list_ok, status);
     list_ok = true;
-    eam_forces_cta<real>(s, n, box, fs, nullptr);
+    eam_forces_cta<real, KMAX == 1>(s, n, box, fs, nullptr);
     bool bad = false;
     if (L.scheme == PMD_SCHEME_PAPER) {
-        double Gc[KMAX][3];
 #pragma unroll
-        for (int k = 0; k < KMAX; ++k) {
-            const int i = threadIdx.x + k * blockDim.x;
+        for (int k = 0; k < KMAX; ++k)
 #pragma unroll
             for (int al = 0; al < 3; ++al) own.vh[k][al] = own.v[k][al];
-            if (i < n) coarse_noise<KMAX>(L, Gpre, nid, 0, i, n, Gc[k]);
-        }
         for (int ell = 0; ell < nsteps; ++ell) {
             const double s0 = sched_sigma(L, ell), s1 = sched_sigma(L, ell + 1);
 #pragma unroll
@@ -508,14 +521,18 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 }
                 s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
             }
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {   // G_{l+1}: this kick and the next step's
+                const int i = threadIdx.x + k * blockDim.x;
+                if (i < n) coarse_noise<KMAX>(L, Gpre, nid, ell + 1, i, n, Gc[k]);
+            }
             __syncthreads();
             eam_refresh_list(s, n, box, fs, false, status);
-            eam_forces_cta<real>(s, n, box, fs, nullptr);
+            eam_forces_cta<real, KMAX == 1>(s, n, box, fs, nullptr);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
                 if (i >= n) break;
-                coarse_noise<KMAX>(L, Gpre, nid, ell + 1, i, n, Gc[k]);   // G_{l+1}: this kick and the next step's
 #pragma unroll
                 for (int al = 0; al < 3; ++al)
                     own.v[k][al] = half_kick(L, own.vh[k][al], s.F[al * n + i], own.vh[k][al], s1, Gc[k][al]);
@@ -527,14 +544,12 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
                 if (i >= n) break;
-                double G[3];
-                coarse_noise<KMAX>(L, Gpre, nid, ell, i, n, G);
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     double v = kick_b(L, own.v[k][al], s.F[al * n + i]);
                     const double q0 = s.q[al * n + i];
                     double q = __dadd_rn(q0, __dmul_rn(L.hdt, v));
-                    v = ou_o(L, v, G[al]);
+                    v = ou_o(L, v, Gc[k][al]);
                     q = __dadd_rn(q, __dmul_rn(L.hdt, v));
                     if (!isfinite(q)) bad = true;
                     if (fabs(q - q0) > 0.5 * box[al]) flag(status, ST_LOSTATOM);
@@ -543,9 +558,14 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 }
                 s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
             }
+#pragma unroll
+            for (int k = 0; k < KMAX; ++k) {   // G_{l+1} for the next step
+                const int i = threadIdx.x + k * blockDim.x;
+                if (i < n && ell + 1 < nsteps) coarse_noise<KMAX>(L, Gpre, nid, ell + 1, i, n, Gc[k]);
+            }
             __syncthreads();
             eam_refresh_list(s, n, box, fs, false, status);
-            eam_forces_cta<real>(s, n, box, fs, nullptr);
+            eam_forces_cta<real, KMAX == 1>(s, n, box, fs, nullptr);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
@@ -588,7 +608,7 @@ __device__ void store_state(const EamShared& s, const OwnState<KMAX>& own, int n
 }
 
 template <typename real, int KMAX>
-__global__ void __launch_bounds__(COARSE_MAX_THREADS) k_coarse_batch(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, double* q, double* v,
+__global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_coarse_batch(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, double* q, double* v,
                                long stride, const int32_t* __restrict__ nsteps, const int64_t* __restrict__ ids,
                                int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -674,7 +694,7 @@ __device__ double cta_max(double x, double* red) {
 }
 
 template <typename real, int KMAX>
-__global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, int nsteps, int n_in,
+__global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_parareal_sweep(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, int nsteps, int n_in,
                                  int n_fin, const double* __restrict__ jumps, const double* __restrict__ prev,
                                  double* __restrict__ cur, double* __restrict__ cout, double delta_expl, int metric,
                                  const double* __restrict__ Gwin, SweepResult* res, int* status) {
@@ -712,48 +732,64 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS) k_parareal_sweep(int n, do
     for (int nn = n_in; nn < n_fin; ++nn) {
         const long idx = nn - n_in;
         const double* Gp = Gwin ? Gwin + (size_t)idx * (nsteps + 1) * 3 * n : nullptr;
-        coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, nsteps, (int64_t)nn, Gp, list_ok, status);
-        __syncthreads();
         double* co = cout + idx * S;
         double* cn = cur + (idx + 1) * S;
         const double* J = jumps ? jumps + idx * S : nullptr;
         const double* P = prev + (idx + 1) * S;
+        // the jump and the previous iterate of the thread's own atom, loaded before the interval
+        // so that they arrive during its force evaluations (one atom per thread: more would
+        // not fit in registers, and those shapes read them after the interval)
+        constexpr bool PRE = KMAX == 1;
+        double Jo[KMAX][6], Po[KMAX][3];
+#pragma unroll
+        for (int k = 0; k < KMAX && PRE; ++k) {
+            const int i = threadIdx.x + k * blockDim.x;
+#pragma unroll
+            for (int c = 0; c < 6; ++c) Jo[k][c] = (J && i < n) ? J[c * n + i] : 0.0;
+#pragma unroll
+            for (int al = 0; al < 3; ++al) Po[k][al] = i < n ? P[al * n + i] : 0.0;
+        }
+        coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, nsteps, (int64_t)nn, Gp, list_ok, status);
+        // jump, writes and error sums on the owning thread of each atom (the force evaluation
+        // ended with a CTA barrier, so no thread still reads q)
         double a = 0.0, b = 0.0, mx = 0.0;
         bool bad = false;
-        for (int x = threadIdx.x; x < 3 * n; x += blockDim.x) {
-            const double c = s.q[x];
-            co[x] = c;
-            const double u = J ? c + J[x] : c;
-            s.q[x] = u;
-            cn[x] = u;
-            if (!isfinite(u)) bad = true;
-        }
 #pragma unroll
         for (int k = 0; k < KMAX; ++k) {
             const int i = threadIdx.x + k * blockDim.x;
             if (i < n) {
+                if (!PRE) {
+#pragma unroll
+                    for (int c = 0; c < 6; ++c) Jo[k][c] = J ? J[c * n + i] : 0.0;
+#pragma unroll
+                    for (int al = 0; al < 3; ++al) Po[k][al] = P[al * n + i];
+                }
+                double d2 = 0.0;
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    const double c = s.q[al * n + i];
+                    co[al * n + i] = c;
+                    const double u = J ? c + Jo[k][al] : c;
+                    s.q[al * n + i] = u;
+                    cn[al * n + i] = u;
+                    if (!isfinite(u)) bad = true;
+                    const double pp = Po[k][al];
+                    d2 += (u - pp) * (u - pp);
+                    b += pp * pp;
+                }
+                a += d2;
+                mx = fmax(mx, d2);
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     const double c = own.v[k][al];
                     co[3 * n + al * n + i] = c;
-                    const double u = J ? c + J[3 * n + al * n + i] : c;
+                    const double u = J ? c + Jo[k][3 + al] : c;
                     own.v[k][al] = u;
                     cn[3 * n + al * n + i] = u;
                     if (!isfinite(u)) bad = true;
                 }
+                s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
             }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            s.qf[i] = wrap_f32(s.q[i], s.q[n + i], s.q[2 * n + i], box);
-            double d2 = 0.0;
-            for (int al = 0; al < 3; ++al) {
-                const double c = s.q[al * n + i], p = P[al * n + i];
-                d2 += (c - p) * (c - p);
-                b += p * p;
-            }
-            a += d2;
-            mx = fmax(mx, d2);
         }
         const int anybad = __syncthreads_or(bad ? 1 : 0);
         if (metric == PMD_METRIC_REL) {
