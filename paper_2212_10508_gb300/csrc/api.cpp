@@ -247,7 +247,7 @@ int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out) {
 int pmd_engine_destroy(pmd_engine* e) {
     if (!e) return PMD_OK;
     DevBuf* bufs[] = {&e->beta, &e->status, &e->s_nbr, &e->s_nnb, &e->s_dedr, &e->s_qf, &e->s_vh, &e->s_order,
-                      &e->s_result, &e->s_noise, &e->s_gstep, &e->s_pos};
+                      &e->s_result, &e->s_noise, &e->s_gstep, &e->s_pos, &e->s_flow};
     for (DevBuf* b : bufs) b->release();
     if (e->pinned) cudaFreeHost(e->pinned);
     if (e->ev0) cudaEventDestroy(e->ev0);
@@ -272,7 +272,8 @@ int pmd_engine_reserve(pmd_engine* e, int nbatch) {
     if ((rc = e->s_nbr.ensure(na * PMD_MAX_NEIGHBORS * sizeof(int))) || (rc = e->s_nnb.ensure(na * sizeof(int))) ||
         (rc = e->s_dedr.ensure(na * PMD_MAX_NEIGHBORS * 3 * rs)) || (rc = e->s_qf.ensure(na * sizeof(float4))) ||
         (rc = e->s_vh.ensure(na * 3 * sizeof(double))) || (rc = e->s_order.ensure((2 * (size_t)nbatch + 4) * sizeof(int))) ||
-        (rc = e->s_gstep.ensure(na * 3 * sizeof(double))))
+        (rc = e->s_gstep.ensure(na * 3 * sizeof(double))) ||
+        (rc = e->s_flow.ensure((2 * (size_t)nbatch + 2) * sizeof(unsigned int))))
         return rc;
     if (e->p.natoms <= PMD_POS_TABLE_MAX_ATOMS && (rc = e->s_pos.ensure((size_t)na * e->p.natoms))) return rc;
     e->cap_batch = nbatch;

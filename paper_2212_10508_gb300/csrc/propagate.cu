@@ -75,6 +75,8 @@ struct FineArgs {
     unsigned char* pos;     // reverse-slot tables [member][n][n], or nullptr (binary search)
     SBShape shape;          // FP32 path: run-time shape of the batched pass
     int b_group;            // atoms per warp in phase B (1..SB_B_GROUP_MAX)
+    unsigned int* flow;     // FP32 path: [0] next item, [1] abort, [2, 2 + nbatch) atoms done in phase A
+                            // per member (order position), [2 + nbatch, 2 + 2 nbatch) in phase B
 };
 
 __global__ void k_fine_prologue(const int32_t* __restrict__ nsteps, int nbatch, int schedule, int* __restrict__ order,
@@ -263,29 +265,11 @@ struct FineNoiseSide {
     }
 };
 
+// FP64 path: warp per atom over the grid, grid barriers between the phases
 template <typename real, int TJ, class SH>
 __device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, long items, const double box[3], int ell) {
     const int n = a.n;
-    if constexpr (sizeof(real) == 4) {
-        // batched design: CTA c takes the contiguous item range [c0, c1) in batches of 32 atoms
-        const long chunk = (items + gridDim.x - 1) / gridDim.x;
-        const long c0 = (long)blockIdx.x * chunk;
-        const long c1 = c0 + chunk < items ? c0 + chunk : items;
-        for (long bs = c0; bs < c1; bs += SB_ATOMS) {
-            const int na = (int)(c1 - bs < SB_ATOMS ? c1 - bs : SB_ATOMS);
-            auto at = [&](int slot) {
-                const long it = bs + slot;
-                const long m = a.order[it / n];
-                const int i = (int)(it % n);
-                const long ai = m * n + i;
-                return SBAtom{a.q + m * a.stride, a.qf + m * n, i, a.nbr + ai * NMAX, a.nnb + ai,
-                              (float*)a.dedr + ai * NMAX * 3, nullptr,
-                              a.pos ? a.pos + ((size_t)m * n + i) * n : nullptr};
-            };
-            const FineNoiseSide side{&a, bs, na, ell};
-            sb_batch<TJ>(sh, sb_tables(a.v), a.v.sp, na, at, n, box, a.status, true, side, a.shape);
-        }
-    } else {
+    {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         const int wpb = blockDim.x >> 5;
         const long gwarp = (long)blockIdx.x * wpb + warp, nwarps = (long)gridDim.x * wpb;
@@ -320,6 +304,131 @@ __device__ __forceinline__ void fine_loop(const FineArgs& a, const SH& sh) {
     }
 }
 
+// ---- FP32 path: dataflow schedule of the sub-steps ------------------------------------------
+// The work of a launch is a fixed sequence of items: for each sub-step ell, the phase-A batches
+// (bA consecutive items of the sub-step's active sequence, the last one partial) and then the
+// phase-B groups (bB consecutive items).  bA = min(SB_ATOMS, ceil(items / CTAs)) and bB =
+// min(16 b_group, ceil(items / CTAs)): a small sub-step is spread over all CTAs (short items on
+// the critical path of one system), a large one is cut into full batches.  CTAs take items from a global counter, in
+// that order, and an item waits only for the members it touches: phase A of ell > 0 for all
+// phase-B work of its members at ell - 1 (their positions are then final, and so is every read of
+// the per-step arrays it overwrites), phase B of ell for all phase-A work of its members at ell
+// (pair derivatives, neighbour lists and Gaussian increments).  Members are independent systems,
+// so a CTA that finishes early goes on with other members' work instead of idling at a grid
+// barrier.  Every wait is for items earlier in the sequence and all CTAs are resident (cooperative
+// launch): the earliest unfinished item never waits, so the schedule cannot deadlock.  No atom's
+// arithmetic depends on the batch it lands in, so the results are those of any other schedule.
+struct FlowCursor {
+    int ell = 0, A = 0;    // sub-step of the window and its active members
+    long base = 0;         // first item of the sub-step
+    long nA = 0, nB = 0;   // its phase-A and phase-B items
+    long bA = 1, bB = 1;   // and their sizes in atoms
+};
+
+__device__ __forceinline__ void flow_set(const FineArgs& a, FlowCursor& c, int bmax) {
+    c.A = c.ell <= *a.Lmax ? active_members(a.Ls, a.nbatch, c.ell) : 0;
+    const long items = (long)c.A * a.n;
+    const long per = (items + gridDim.x - 1) / gridDim.x;
+    c.bA = per < SB_ATOMS ? (per > 0 ? per : 1) : SB_ATOMS;
+    c.bB = per < bmax ? (per > 0 ? per : 1) : bmax;
+    c.nA = (items + c.bA - 1) / c.bA;
+    c.nB = (items + c.bB - 1) / c.bB;
+}
+
+// Thread 0: wait until *ctr >= target (bounded; the abort word ends every wait of the launch).
+__device__ __forceinline__ bool flow_wait(const FineArgs& a, unsigned int* ctr, unsigned int target) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> x(*ctr), ab(a.flow[1]);
+    // about 4 s at ~200 ns per poll, far above any legitimate wait (one item takes < 1 ms)
+    const long long limit = 20000000LL;
+    long long it = 0;
+    while (x.load(cuda::memory_order_acquire) < target) {
+        if (ab.load(cuda::memory_order_relaxed) != 0) return false;
+        if (++it > limit) {
+            ab.store(1u, cuda::memory_order_relaxed);
+            flag(a.status, ST_TIMEOUT);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+template <int TJ>
+__device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
+    __shared__ long s_item[4];   // sub-step, phase (0 A, 1 B, -1 done), items [first, end)
+    const int n = a.n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
+    const int bmax = nw * a.b_group;   // phase-B item: at most b_group atoms per warp
+    const double box[3] = {a.box0, a.box1, a.box2};
+    unsigned int* doneA = a.flow + 2;
+    unsigned int* doneB = a.flow + 2 + a.nbatch;
+    FlowCursor c;   // thread 0's view of the sequence (items are taken in increasing order)
+    if (threadIdx.x == 0) flow_set(a, c, bmax);
+    for (;;) {
+        if (threadIdx.x == 0) {
+            cuda::atomic_ref<unsigned int, cuda::thread_scope_device> head(a.flow[0]), ab(a.flow[1]);
+            const long t = ab.load(cuda::memory_order_relaxed) != 0 ? -1 : (long)head.fetch_add(1u, cuda::memory_order_relaxed);
+            while (t >= 0 && c.A > 0 && t >= c.base + c.nA + c.nB) {
+                c.base += c.nA + c.nB;
+                ++c.ell;
+                flow_set(a, c, bmax);
+            }
+            const long items = (long)c.A * n;
+            int ph = -1;
+            long s = 0, e = 0;
+            if (t >= 0 && c.A > 0) {
+                const long r = t - c.base;
+                ph = r < c.nA ? 0 : 1;
+                s = ph == 0 ? r * c.bA : (r - c.nA) * c.bB;
+                e = s + (ph == 0 ? c.bA : c.bB);
+                if (e > items) e = items;
+            }
+            // wait for the members of [s, e): A of ell > 0 on their phase B of ell - 1, B on their phase A
+            bool ok = true;
+            if (ph >= 0 && !(ph == 0 && c.ell == 0)) {
+                for (long p = s / n; p <= (e - 1) / n && ok; ++p)
+                    ok = ph == 0 ? flow_wait(a, doneB + p, (unsigned int)((long)c.ell * n))
+                                 : flow_wait(a, doneA + p, (unsigned int)((long)(c.ell + 1) * n));
+            }
+            s_item[0] = c.ell;
+            s_item[1] = ok ? ph : -1;
+            s_item[2] = s;
+            s_item[3] = e;
+        }
+        __syncthreads();
+        const int ell = (int)s_item[0];
+        const int ph = (int)s_item[1];
+        const long s = s_item[2], e = s_item[3];
+        if (ph < 0) return;
+        // both branches end with a CTA barrier, after which thread 0 may rewrite s_item
+        if (ph == 0) {
+            const int na = (int)(e - s);
+            auto at = [&](int slot) {
+                const long it = s + slot;
+                const long m = a.order[it / n];
+                const int i = (int)(it % n);
+                const long ai = m * n + i;
+                return SBAtom{a.q + m * a.stride, a.qf + m * n, i, a.nbr + ai * NMAX, a.nnb + ai,
+                              (float*)a.dedr + ai * NMAX * 3, nullptr,
+                              a.pos ? a.pos + ((size_t)m * n + i) * n : nullptr};
+            };
+            const FineNoiseSide side{&a, s, na, ell};
+            sb_batch<TJ>(sh, sb_tables(a.v), a.v.sp, na, at, n, box, a.status, true, side, a.shape);   // ends with a barrier
+        } else {
+            if (s + warp < e) fine_phase_b<float>(a, s + warp, nw, e, ell, lane);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {   // publish: the item's atoms per member
+            unsigned int* done = ph == 0 ? doneA : doneB;
+            for (long p = s / n; p <= (e - 1) / n; ++p) {
+                const long lo = p * n > s ? p * n : s, hi = (p + 1) * n < e ? (p + 1) * n : e;
+                cuda::atomic_ref<unsigned int, cuda::thread_scope_device> x(done[p]);
+                x.fetch_add((unsigned int)(hi - lo), cuda::memory_order_release);
+            }
+        }
+    }
+}
+
 template <typename real, int TJ>
 __global__ void __launch_bounds__(snap_cta_threads<real>(), 1) k_fine_persistent(FineArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -327,7 +436,7 @@ __global__ void __launch_bounds__(snap_cta_threads<real>(), 1) k_fine_persistent
         SBShared<TJ> sh = sb_shared_carve<TJ>(smem, a.v);
         sb_shared_load<TJ>(sh, a.v);
         __syncthreads();
-        fine_loop<real, TJ>(a, sh);
+        fine_flow<TJ>(a, sh);
     } else {
         SnapShared<real, TJ> sh = snap_shared_carve<real, TJ>(smem, a.v);
         snap_shared_load<real, TJ>(sh, a.v);
@@ -370,7 +479,9 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
     unsigned int* words = reinterpret_cast<unsigned int*>(e->status.as<int>() + 1);
     a.bar = words;
     a.status = e->status.as<int>();
+    a.flow = e->s_flow.as<unsigned int>();
     PMD_CUDA_TRY(cudaMemsetAsync(words, 0, 4 * sizeof(unsigned int), st));
+    if (sizeof(real) == 4) PMD_CUDA_TRY(cudaMemsetAsync(a.flow, 0, (2 * (size_t)nbatch + 2) * sizeof(unsigned int), st));
     k_fine_prologue<<<1, 1024, 0, st>>>(nsteps, nbatch, lp.schedule, e->s_order.as<int>(), (int*)a.Ls, (int*)a.Lmax,
                                         a.status);
     PMD_CUDA_TRY(cudaGetLastError());
