@@ -193,6 +193,13 @@ int pmd_sync_status(pmd_engine* e, pmd_stream_t stream);
  * receives the duration of the most recent such kernel (waits for it to finish), or -1 if none. */
 int pmd_engine_profile(pmd_engine* e, int enable, double* last_ms);
 
+/* Self-test of the bounded cross-CTA waits (failure detection without a GPU fault): launches one
+ * CTA that waits on a counter nothing increments (the wait of the fine kernel's dataflow
+ * schedule) and then on a two-CTA grid barrier with only itself launched (the barrier of the
+ * FP64 path), each for at most `polls` polls (>= 1; ~200 ns each).  Both give up, and the next
+ * pmd_sync_status returns PMD_ETIMEOUT; the engine stays usable.  EINVAL for polls < 1. */
+int pmd_engine_selftest_waits(pmd_engine* e, long long polls, pmd_stream_t stream);
+
 /* Run-time shape of the batched FP32 fine kernel (the FP64 form ignores it):
  *   rows2_atoms  batches of at most this many atoms (0..16) run the Y contraction with two output
  *                rows per warp (half-warps of 16 atoms), rows4_atoms (0..8) with four rows per warp;

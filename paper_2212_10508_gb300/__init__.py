@@ -77,7 +77,7 @@ EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_nu
            "pmd_snap_reserve",
            "snap_energy_forces", "pmd_snap_sync_status", "snap_energy_forces_noalloc", "eam_energy_forces", "pmd_engine_create",
            "pmd_engine_destroy", "pmd_engine_set_beta", "pmd_engine_reserve", "pmd_engine_profile", "pmd_sync_status",
-           "pmd_engine_get_tuning", "pmd_engine_set_tuning", "pmd_engine_autotune",
+           "pmd_engine_selftest_waits", "pmd_engine_get_tuning", "pmd_engine_set_tuning", "pmd_engine_autotune",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
            "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log"]
 
@@ -110,6 +110,7 @@ def lib():
     L.pmd_engine_set_beta.argtypes = [vp, vp, vp]
     L.pmd_engine_reserve.argtypes = [vp, i32]
     L.pmd_engine_profile.argtypes = [vp, i32, dp]
+    L.pmd_engine_selftest_waits.argtypes = [vp, i64, vp]
     L.pmd_sync_status.argtypes = [vp, vp]
     L.pmd_engine_get_tuning.argtypes = [vp, ctypes.POINTER(FineTuning)]
     L.pmd_engine_set_tuning.argtypes = [vp, ctypes.POINTER(FineTuning)]
@@ -133,13 +134,17 @@ def _check(rc):
         raise PmdError(rc, lib().pmd_last_error().decode())
 
 
-def _ptr(t):
-    """Device pointer of a CUDA tensor (or None)."""
+def _ptr(t, dtype="f64"):
+    """Device pointer of a contiguous CUDA tensor of the given element type ("f64", "i32" or
+    "i64"; the C ABI reads the bytes as that type), or None."""
     if t is None:
         return None
     import torch
-    if not (t.is_cuda and t.dtype in (torch.float64, torch.int32, torch.int64) and t.is_contiguous()):
-        raise ValueError("expected a contiguous CUDA tensor of float64/int32/int64")
+    want = {"f64": torch.float64, "i32": torch.int32, "i64": torch.int64}[dtype]
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    if t.dtype != want:
+        raise TypeError("expected a %s tensor, got %s" % (want, t.dtype))
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -248,6 +253,10 @@ class Engine:
     def sync_status(self, stream=None):
         _check(lib().pmd_sync_status(self.h, _stream(stream)))
 
+    def selftest_waits(self, polls=1000, stream=None):
+        """Run the bounded-wait self-test; the next sync_status raises PmdError(ETIMEOUT)."""
+        _check(lib().pmd_engine_selftest_waits(self.h, int(polls), _stream(stream)))
+
     def profile(self, enable=True):
         """Enable/disable kernel timing; returns the last persistent-kernel duration in ms (or -1)."""
         ms = ctypes.c_double()
@@ -275,7 +284,7 @@ class Engine:
         else:
             qp, vp, stride = _ptr(q), _ptr(v), 3 * self.natoms
         t, ms = FineTuning(), ctypes.c_double()
-        _check(lib().pmd_engine_autotune(self.h, nb, self.natoms, qp, vp, stride, _ptr(nsteps), _ptr(interval_id),
+        _check(lib().pmd_engine_autotune(self.h, nb, self.natoms, qp, vp, stride, _ptr(nsteps, "i32"), _ptr(interval_id, "i64"),
                                          ctypes.byref(lp), int(max_steps), _stream(stream), ctypes.byref(t),
                                          ctypes.byref(ms)))
         return t.as_dict(), ms.value
@@ -292,7 +301,7 @@ class Engine:
         else:
             qp, vp, stride = _ptr(q), _ptr(v), 3 * self.natoms
         _check(lib().baoab_propagate_batch(self.h, potential, nb, self.natoms, qp, vp, stride,
-                                           _ptr(nsteps), _ptr(interval_id), ctypes.byref(lp), _stream(stream)))
+                                           _ptr(nsteps, "i32"), _ptr(interval_id, "i64"), ctypes.byref(lp), _stream(stream)))
 
     def parareal_jumps(self, count, fine_out, coarse_prev, jumps, stream=None):
         _check(lib().parareal_jumps(self.h, count, _ptr(fine_out), _ptr(coarse_prev), _ptr(jumps), _stream(stream)))

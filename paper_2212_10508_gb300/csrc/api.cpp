@@ -117,6 +117,7 @@ static int read_status(int* dstatus, cudaStream_t st) {
     return status_to_code(h);
 }
 
+int selftest_waits(pmd_engine* e, long long polls, cudaStream_t st);
 }  // namespace pmd
 
 using namespace pmd;
@@ -247,7 +248,8 @@ int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out) {
 int pmd_engine_destroy(pmd_engine* e) {
     if (!e) return PMD_OK;
     DevBuf* bufs[] = {&e->beta, &e->status, &e->s_nbr, &e->s_nnb, &e->s_dedr, &e->s_qf, &e->s_vh, &e->s_order,
-                      &e->s_result, &e->s_noise, &e->s_gstep, &e->s_pos, &e->s_flow};
+                      &e->s_result, &e->s_noise, &e->s_gstep, &e->s_pos, &e->s_flow,
+                      &e->s_selftest};
     for (DevBuf* b : bufs) b->release();
     if (e->pinned) cudaFreeHost(e->pinned);
     if (e->ev0) cudaEventDestroy(e->ev0);
@@ -278,6 +280,11 @@ int pmd_engine_reserve(pmd_engine* e, int nbatch) {
     if (e->p.natoms <= PMD_POS_TABLE_MAX_ATOMS && (rc = e->s_pos.ensure((size_t)na * e->p.natoms))) return rc;
     e->cap_batch = nbatch;
     return PMD_OK;
+}
+
+int pmd_engine_selftest_waits(pmd_engine* e, long long polls, pmd_stream_t stream) {
+    if (!e || polls < 1) return fail(PMD_EINVAL, "pmd_engine_selftest_waits: need an engine and polls >= 1");
+    return selftest_waits(e, polls, (cudaStream_t)stream);
 }
 
 int pmd_engine_profile(pmd_engine* e, int enable, double* last_ms) {

@@ -94,7 +94,28 @@ struct GridBarrier {
     unsigned int nblocks;
 };
 
-__device__ __forceinline__ bool grid_sync(GridBarrier gb, int* status, int timeout_bit) {
+// Spin limit of every cross-CTA wait: about 4 s at ~200 ns per poll, far above any legitimate wait.
+constexpr long long WAIT_POLLS = 20000000LL;
+
+// One thread: wait until *ctr >= target, at most `limit` polls.  The abort word ends the wait at
+// once (false); running out of polls sets the abort word and the status bit and returns false.
+__device__ __forceinline__ bool bounded_wait_geq(unsigned int* ctr, unsigned int target, unsigned int* abort_word,
+                                                 int* status, int timeout_bit, long long limit = WAIT_POLLS) {
+    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> x(*ctr), ab(*abort_word);
+    long long it = 0;
+    while (x.load(cuda::memory_order_acquire) < target) {
+        if (ab.load(cuda::memory_order_relaxed) != 0) return false;
+        if (++it > limit) {
+            ab.store(1u, cuda::memory_order_relaxed);
+            flag(status, timeout_bit);
+            return false;
+        }
+        __nanosleep(64);
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool grid_sync(GridBarrier gb, int* status, int timeout_bit, long long limit = WAIT_POLLS) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -109,8 +130,6 @@ __device__ __forceinline__ bool grid_sync(GridBarrier gb, int* status, int timeo
                 cnt.store(0u, cuda::memory_order_relaxed);
                 gen.fetch_add(1u, cuda::memory_order_acq_rel);
             } else {
-                // about 4 s at ~200 ns per poll, far above any legitimate wait
-                const long long limit = 20000000LL;
                 long long it = 0;
                 while (gen.load(cuda::memory_order_acquire) == g) {
                     if (abrt.load(cuda::memory_order_relaxed) != 0) {

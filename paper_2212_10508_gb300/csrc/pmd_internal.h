@@ -116,6 +116,7 @@ struct pmd_engine {
     pmd::DevBuf status;              // int status word + barrier words
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_vh, s_order, s_Ls, s_result;
     pmd::DevBuf s_noise;             // Gaussian increments of a parareal_correct window
+    pmd::DevBuf s_selftest;          // words of pmd_engine_selftest_waits
     pmd::DevBuf s_flow;              // FP32 fine path: item counter, abort word, per-member phase counters
     pmd::DevBuf s_gstep;             // Gaussian increments of one fine sub-step [item][3] (FP32 path)
     pmd::DevBuf s_pos;               // reverse neighbour slots [member][j][k] (uint8), natoms <= PMD_POS_TABLE_MAX_ATOMS

@@ -335,22 +335,31 @@ __device__ __forceinline__ void flow_set(const FineArgs& a, FlowCursor& c, int b
     c.nB = (items + c.bB - 1) / c.bB;
 }
 
-// Thread 0: wait until *ctr >= target (bounded; the abort word ends every wait of the launch).
+// Thread 0: wait until *ctr >= target (bounded; one item takes < 1 ms, the limit ~4 s; the abort
+// word ends every wait of the launch).
 __device__ __forceinline__ bool flow_wait(const FineArgs& a, unsigned int* ctr, unsigned int target) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> x(*ctr), ab(a.flow[1]);
-    // about 4 s at ~200 ns per poll, far above any legitimate wait (one item takes < 1 ms)
-    const long long limit = 20000000LL;
-    long long it = 0;
-    while (x.load(cuda::memory_order_acquire) < target) {
-        if (ab.load(cuda::memory_order_relaxed) != 0) return false;
-        if (++it > limit) {
-            ab.store(1u, cuda::memory_order_relaxed);
-            flag(a.status, ST_TIMEOUT);
-            return false;
-        }
-        __nanosleep(64);
-    }
-    return true;
+    return bounded_wait_geq(ctr, target, a.flow + 1, a.status, ST_TIMEOUT);
+}
+
+// Self-test of the bounded waits: one CTA waits on a counter that nothing increments (the
+// scheduler's wait) and then on a grid barrier of two CTAs with only itself launched (the FP64
+// path's barrier); both must give up after `polls` polls with ST_TIMEOUT.  words: [0] counter,
+// [1] abort word of the first wait, [2..5] barrier words.
+__global__ void k_selftest_waits(unsigned int* words, int* status, long long polls) {
+    if (threadIdx.x == 0) bounded_wait_geq(words, 1u, words + 1, status, ST_TIMEOUT, polls);
+    __syncthreads();
+    const GridBarrier gb{words + 2, 2u};
+    grid_sync(gb, status, ST_TIMEOUT, polls);
+}
+
+int selftest_waits(pmd_engine* e, long long polls, cudaStream_t st) {
+    int rc;
+    if ((rc = e->s_selftest.ensure(8 * sizeof(unsigned int)))) return rc;
+    unsigned int* w = e->s_selftest.as<unsigned int>();
+    PMD_CUDA_TRY(cudaMemsetAsync(w, 0, 8 * sizeof(unsigned int), st));
+    k_selftest_waits<<<1, 32, 0, st>>>(w, e->status.as<int>(), polls);
+    PMD_CUDA_TRY(cudaGetLastError());
+    return PMD_OK;
 }
 
 template <int TJ>

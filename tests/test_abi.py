@@ -58,6 +58,7 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.pmd_engine_set_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
     assert lib.pmd_engine_get_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
     assert lib.pmd_engine_autotune(None, 1, 1, None, None, 3, None, None, None, 1, None, None, None) == P.PMD_EINVAL
+    assert lib.pmd_engine_selftest_waits(None, 100, None) == P.PMD_EINVAL
 
 
 def _replay(N, dc, de, trace):

@@ -138,3 +138,40 @@ def test_fine_propagation_replays_from_a_cuda_graph():
         torch.cuda.synchronize()
         eng.sync_status()
         assert torch.equal(qg, q1) and torch.equal(vg, v1)
+
+
+def test_bounded_waits_time_out_and_engine_stays_usable():
+    """The cross-CTA waits give up after their poll limit with ETIMEOUT (a counter nothing
+    increments, a grid barrier missing a CTA), and the engine then propagates as before."""
+    q, v, box, beta = _system(4, 2, 1000.0, 16)
+    L = np.array([3, 2], dtype=np.int32)
+    ids = np.array([5, 6], dtype=np.int64)
+    eng = P.Engine(q.shape[2], box, beta=T(beta))
+    lp = P.langevin(T=1000.0)
+    q1, v1 = T(q), T(v)
+    eng.baoab_propagate_batch(P.FINE, q1, v1, T(L, torch.int32), T(ids, torch.int64), lp)
+    eng.sync_status()
+    eng.selftest_waits(polls=1000)
+    with pytest.raises(P.PmdError) as e:
+        eng.sync_status()
+    assert e.value.code == P.PMD_ETIMEOUT
+    eng.sync_status()   # cleared
+    q2, v2 = T(q), T(v)
+    eng.baoab_propagate_batch(P.FINE, q2, v2, T(L, torch.int32), T(ids, torch.int64), lp)
+    eng.sync_status()
+    assert torch.equal(q1, q2) and torch.equal(v1, v2)
+    with pytest.raises(P.PmdError):
+        eng.selftest_waits(polls=0)
+
+
+def test_mistyped_step_counts_and_ids_are_rejected():
+    """The binding checks element types before anything is launched (the C ABI reads the bytes
+    as int32 step counts and int64 interval ids)."""
+    q, v, box, beta = _system(4, 2, 1000.0, 17)
+    eng = P.Engine(q.shape[2], box, beta=T(beta))
+    lp = P.langevin(T=1000.0)
+    gq, gv = T(q), T(v)
+    for L, ids in ((T([3, 2]), T([5, 6], torch.int64)), (T([3, 2], torch.int32), T([5, 6], torch.int32))):
+        with pytest.raises(TypeError):
+            eng.baoab_propagate_batch(P.FINE, gq, gv, L, ids, lp)
+    assert torch.equal(gq, T(q)) and torch.equal(gv, T(v))
