@@ -301,6 +301,38 @@ int pmd_adaptive_cost(const pmd_adaptive* st, double C_f, double C_c, double* co
  * k^{s,j} and the slab index s (0-based).  Returns the count, or < 0 on error. */
 int pmd_adaptive_log(const pmd_adaptive* st, int capacity, int* n_init, int* n_final, int* k, int* slab);
 
+/* ---- SIA tracking (Sec. 3: location of the self-interstitial and its residence times) --------
+ * The paper locates the interstitial by a Voronoi analysis of each frame and reports residence
+ * times in a well in units of the time step (Sec. 3, the table of residence times, and the
+ * statistical study that follows it).  Reading used here (Wigner-Seitz): every atom belongs to
+ * its nearest site of a reference lattice shifted by the centre-of-mass displacement of the
+ * frame; the interstitial's well is the site with the largest occupancy (2 for one interstitial;
+ * the smallest site index on ties).
+ *
+ * sia_locate: frame f of `frames` starts at frames + f * frame_stride (doubles; >= 3 natoms) and
+ * holds unwrapped positions [3][natoms] in Angstrom (so the states [N+1][6][natoms] of a parareal
+ * run are frames with stride 6 natoms).  ref [3][natoms] are the positions the centre-of-mass
+ * displacement is taken from (usually frame 0), sites [3][nsites] the reference lattice (device
+ * pointers); box [3] is host memory.  Per frame, in FP64 with this rounding order (the same in any
+ * implementation, so that every nearest-site decision is reproducible bit for bit):
+ *   c_a   = (sum over i in index order of (q_ai - ref_ai)) / natoms          for a = x, y, z
+ *   d_a   = ((q_ai - c_a) - s_a), then d_a -= L_a * rint(d_a / L_a)
+ *   r2    = (d_x d_x + d_y d_y) + d_z d_z, no fused multiply-adds
+ *   site  = the smallest index with the smallest r2.
+ * Outputs (device, [nframes] int32): well[f] and occupancy[f] = the number of atoms on that site.
+ * Asynchronous on `stream`.  EINVAL: nframes < 0, natoms < 1, nsites < 1 or > 4096, a NULL array
+ * (when nframes > 0), frame_stride < 3 natoms, or a non-positive box length. */
+int sia_locate(int nframes, int natoms, int nsites, const double box[3], const double* frames,
+               int64_t frame_stride, const double* ref, const double* sites, int32_t* well,
+               int32_t* occupancy, pmd_stream_t stream);
+
+/* Residence times of a well sequence (host arrays): the lengths, in frames, of the runs of equal
+ * consecutive wells, in order; the last run is still open at the end of the sequence and is not
+ * returned (its length is a lower bound).  lengths and sites (may be NULL) receive at most
+ * `capacity` entries; *nruns the number of completed runs.  EINVAL for NULL well / nruns or
+ * nframes < 0; ENOMEM (nothing written beyond capacity) if capacity is too small. */
+int sia_residence(const int32_t* well, int nframes, int capacity, int32_t* lengths, int32_t* sites, int* nruns);
+
 #ifdef __cplusplus
 }
 #endif

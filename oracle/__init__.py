@@ -11,6 +11,8 @@ Contents:
     product-rule gradient, the Langevin schemes of eqs. (2)-(3)/(11)-(12) and BAOAB.
   * ``oracle.parareal``: Alg. 1 (classical parareal), Alg. 2 (adaptive parareal) and
     the cost / gain model of eqs. (7)-(9), written in the paper's order and notation.
+  * ``oracle.sia``: the interstitial's well in each frame (Wigner-Seitz reading of the
+    Voronoi analysis of Sec. 3) and its residence times.
 
 Parity status of each function is listed in the module docstrings; the Philox bit
 stream itself is "parity unpinned" against published known-answer vectors (none are

@@ -13,6 +13,8 @@ CPU fallback); build it with ``python -m paper_2212_10508_gb300.build``.
 import ctypes
 import os
 
+import numpy as np
+
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libpmd.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pmd.h")
@@ -79,7 +81,8 @@ EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_nu
            "pmd_engine_destroy", "pmd_engine_set_beta", "pmd_engine_reserve", "pmd_engine_profile", "pmd_sync_status",
            "pmd_engine_selftest_waits", "pmd_engine_get_tuning", "pmd_engine_set_tuning", "pmd_engine_autotune",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
-           "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log"]
+           "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log", "sia_locate",
+           "sia_residence"]
 
 _lib = None
 
@@ -125,6 +128,8 @@ def lib():
     L.adaptive_restart.argtypes = [vp, ctypes.c_double, i32, ctypes.POINTER(Action)]
     L.pmd_adaptive_cost.argtypes = [vp, ctypes.c_double, ctypes.c_double, dp, dp, dp]
     L.pmd_adaptive_log.argtypes = [vp, i32, ip, ip, ip, ip]
+    L.sia_locate.argtypes = [i32, i32, i32, dp, vp, i64, vp, vp, vp, vp, vp]
+    L.sia_residence.argtypes = [vp, i32, i32, vp, vp, ip]
     _lib = L
     return L
 
@@ -211,6 +216,36 @@ def snap_energy_forces(snap: Snap, pos, box, beta, energy=True, forces=True, sum
     _check(lib().snap_energy_forces(snap.h, nb, n, _box(box), _ptr(pos), _ptr(beta), _ptr(E), _ptr(F), _ptr(S),
                                     _stream(stream)))
     return E, F, S
+
+
+def sia_locate(frames, ref, sites, box, stream=None):
+    """Well of the self-interstitial in every frame (Wigner-Seitz: most occupied site of the
+    reference lattice `sites` [3,nsites] shifted by the frame's centre-of-mass displacement from
+    `ref` [3,n]).  frames [nf, rows, n] float64 with the positions in rows 0..2 (rows = 3, or 6
+    for the states of a parareal run).  Returns (well, occupancy), int32 [nf] CUDA tensors."""
+    import torch
+    nf, rows, n = frames.shape
+    if rows < 3:
+        raise ValueError("frames need at least 3 rows (positions)")
+    well = torch.empty(nf, dtype=torch.int32, device=frames.device)
+    occ = torch.empty(nf, dtype=torch.int32, device=frames.device)
+    _check(lib().sia_locate(nf, n, sites.shape[1], _box(box), _ptr(frames), rows * n, _ptr(ref), _ptr(sites),
+                            _ptr(well, "i32"), _ptr(occ, "i32"), _stream(stream)))
+    return well, occ
+
+
+def sia_residence(well):
+    """Completed residence times (frames) of a well sequence and the well of each residence
+    (the last, still open, run is left out): (lengths, sites) as int32 numpy arrays."""
+    w = well.detach().cpu().numpy() if hasattr(well, "detach") else well
+    w = np.ascontiguousarray(w, dtype=np.int32)
+    nf = int(w.shape[0])
+    lengths = np.empty(max(nf, 1), np.int32)
+    sites = np.empty(max(nf, 1), np.int32)
+    k = ctypes.c_int()
+    _check(lib().sia_residence(w.ctypes.data_as(ctypes.c_void_p), nf, nf, lengths.ctypes.data_as(ctypes.c_void_p),
+                               sites.ctypes.data_as(ctypes.c_void_p), ctypes.byref(k)))
+    return lengths[:k.value].copy(), sites[:k.value].copy()
 
 
 def eam_energy_forces(pos, box, params: FSParams = None, energy=True, forces=True, stream=None):

@@ -59,6 +59,22 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.pmd_engine_get_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
     assert lib.pmd_engine_autotune(None, 1, 1, None, None, 3, None, None, None, 1, None, None, None) == P.PMD_EINVAL
     assert lib.pmd_engine_selftest_waits(None, 100, None) == P.PMD_EINVAL
+    box3 = (ctypes.c_double * 3)(10.0, 10.0, 10.0)
+    assert lib.sia_locate(1, 0, 4, box3, None, 3, None, None, None, None, None) == P.PMD_EINVAL
+    assert lib.sia_locate(1, 4, 0, box3, None, 12, None, None, None, None, None) == P.PMD_EINVAL
+    assert lib.sia_locate(1, 4, 4097, box3, None, 12, None, None, None, None, None) == P.PMD_EINVAL
+    assert lib.sia_locate(1, 4, 4, box3, None, 12, None, None, None, None, None) == P.PMD_EINVAL
+    assert lib.sia_locate(0, 4, 4, box3, None, 12, None, None, None, None, None) == P.PMD_OK
+    bad = (ctypes.c_double * 3)(10.0, 0.0, 10.0)
+    assert lib.sia_locate(0, 4, 4, bad, None, 12, None, None, None, None, None) == P.PMD_EINVAL
+    k = ctypes.c_int()
+    assert lib.sia_residence(None, 3, 3, None, None, ctypes.byref(k)) == P.PMD_EINVAL
+    w = (ctypes.c_int32 * 5)(1, 1, 2, 2, 3)
+    L = (ctypes.c_int32 * 1)()
+    assert lib.sia_residence(w, 5, 1, L, None, ctypes.byref(k)) == P.PMD_ENOMEM
+    L2 = (ctypes.c_int32 * 5)()
+    assert lib.sia_residence(w, 5, 5, L2, None, ctypes.byref(k)) == P.PMD_OK and k.value == 2
+    assert list(L2)[:2] == [2, 2]
 
 
 def _replay(N, dc, de, trace):

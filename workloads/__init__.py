@@ -139,3 +139,44 @@ def batch_workload(master=2212, nbatch=64, T=1500.0, lo=100, hi=2000, ncell=4, s
     L = interval_lengths(nbatch, rng(master, 13), lo, hi)
     ids = np.arange(nbatch, dtype=np.int64)
     return q, v, box, beta, L, ids
+
+
+def sia_frames(ncell, nframes, gen: np.random.Generator, sigma=0.08, hop=0.05, drift=0.05, images=True,
+               a: float = A_W, split: float = 1.1):
+    """Synthetic interstitial trajectory for the tracking tests: atoms keep their identity; the
+    doubly occupied site (a <111> dumbbell, orientation sign drawn per frame) hops with
+    probability `hop` per frame by moving one of its two atoms to one of the 8 nearest-neighbour
+    sites (which then holds the new dumbbell); every frame adds i.i.d. N(0, sigma^2) displacements and a common drift
+    (a Gaussian random walk with step `drift` per coordinate); if `images`, every atom's
+    coordinates carry fixed box-vector offsets (-1, 0, +1), as unwrapped coordinates do.  Returns (frames [nf, 3, n], sites [3, ns],
+    box, intended wells [nf])."""
+    sites, box = bcc(ncell, a)
+    ns = sites.shape[1]
+    s0 = int(gen.integers(ns))
+    home = np.concatenate([np.arange(ns), [s0]])          # atom i sits on site home[i]
+    n = ns + 1
+    u = np.ones(3) / np.sqrt(3.0)
+    frames = np.empty((nframes, 3, n))
+    wells = np.empty(nframes, np.int32)
+    shift = np.zeros(3)
+    offs = box[:, None] * gen.integers(-1, 2, size=(3, n)) if images else np.zeros((3, n))
+    for f in range(nframes):
+        if f > 0 and gen.random() < hop:
+            w0 = wells[f - 1]
+            pair = np.flatnonzero(home == w0)
+            dd = sites - sites[:, w0:w0 + 1]
+            dd -= box[:, None] * np.rint(dd / box[:, None])
+            near = np.flatnonzero(np.abs(np.sqrt(np.sum(dd * dd, axis=0)) - a * np.sqrt(3.0) / 2) < 1e-6)
+            home[pair[int(gen.integers(2))]] = int(near[int(gen.integers(near.size))])
+        cnt = np.bincount(home, minlength=ns)
+        w = int(np.flatnonzero(cnt == 2)[0])
+        wells[f] = w
+        q = sites[:, home].copy()
+        pair = np.flatnonzero(home == w)
+        sign = 1.0 if gen.random() < 0.5 else -1.0
+        q[:, pair[0]] += sign * split * u
+        q[:, pair[1]] -= sign * split * u
+        if f > 0:
+            shift = shift + gen.normal(0.0, drift, size=3)
+        frames[f] = q + shift[:, None] + gen.normal(0.0, sigma, size=q.shape) + offs
+    return frames, sites, box, wells
