@@ -36,18 +36,22 @@ WORKLOAD = ("batched fine propagation: 64 intervals x 129-atom W+SIA cell, SNAP 
 SMALL = "profiling case: the same 64 intervals with L_b ~ U{5..20}"
 # DRAM bytes (read + write) of one full-size launch of the persistent FP32 kernel, from one ncu
 # capture of this workload (profiles/fine_persistent_batch64_dram.md), valid only for the kernel
-# sources it was taken on (fingerprint of paper_2212_10508_gb300/csrc); reported as null otherwise.
-TRAFFIC = {"bytes_per_launch": 3.46e6 + 43.62e6, "csrc_sha256_16": "b9a056306950ae7a"}
+# sources it was taken on (fingerprint of the persistent kernel's translation unit and of the host
+# code that builds its tables); reported as null otherwise.
+TRAFFIC = {"bytes_per_launch": 3.46e6 + 43.62e6, "csrc_sha256_16": "7a485281e88635fe"}
+
+
+KERNEL_SOURCES = ("propagate.cu", "snap.cu", "snap_kernels.cuh", "snap_batch.cuh", "snap_v2.cuh", "snap_device.cuh",
+                  "device_common.cuh", "langevin_device.cuh", "eam_device.cuh", "pmd_internal.h", "status_bits.h")
 
 
 def _csrc_fingerprint():
-    import glob
     import hashlib
     d = os.path.join(ROOT, "paper_2212_10508_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(glob.glob(d + "/*.cu") + glob.glob(d + "/*.cuh") + glob.glob(d + "/*.h") + glob.glob(d + "/*.cpp")):
-        h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES:
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
