@@ -2,10 +2,12 @@
 //
 //  * FINE (SNAP): one persistent cooperative kernel runs every member's sub-steps.  Members
 //    are sorted by their number of steps (longest first) so that the members still active at
-//    sub-step l form a prefix; each sub-step is two grid-wide phases separated by bounded
-//    grid barriers: (A) one warp per active atom builds its neighbour list and its pair
-//    derivatives dE_i/dr_ik, (B) one thread per active atom gathers its force and advances
-//    the Langevin scheme.  Uneven interval lengths cost nothing beyond the active prefix.
+//    sub-step l form a prefix.  Each sub-step has two phases: (A) neighbour lists and pair
+//    derivatives dE_i/dr_ik of the active atoms (FP32: batches of up to 32 atoms per CTA; FP64:
+//    one warp per atom), (B) the force gather and the Langevin update.  The FP32 path runs them
+//    as a dataflow schedule with per-member dependencies (fine_flow), the FP64 path with bounded
+//    grid barriers between the phases (fine_loop).  Uneven interval lengths cost nothing beyond
+//    the active prefix.
 //  * COARSE (EAM): one CTA per member runs the whole interval in shared memory.
 //  * parareal_correct: one CTA walks the window sequentially (Algorithm 2's inner loop) with
 //    the same per-CTA coarse code, so C(cur_n) here equals C(prev_n) of the batched path bit
