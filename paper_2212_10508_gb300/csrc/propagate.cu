@@ -271,18 +271,16 @@ struct FineNoiseSide {
 template <typename real, int TJ, class SH>
 __device__ __forceinline__ void fine_phase_a(const FineArgs& a, const SH& sh, long items, const double box[3], int ell) {
     const int n = a.n;
-    {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        const int wpb = blockDim.x >> 5;
-        const long gwarp = (long)blockIdx.x * wpb + warp, nwarps = (long)gridDim.x * wpb;
-        for (long it = gwarp; it < items; it += nwarps) {
-            const int m = a.order[it / n];
-            const int i = (int)(it % n);
-            real* dd = (real*)a.dedr + ((long)m * n + i) * NMAX * 3;
-            snap_atom_warp2<real, TJ>(sh.ws[warp], sh.tab, a.v.yt, sh.cg, sh.beff, a.v.sp, lane, n, i, a.q + m * a.stride,
-                                      a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX,
-                                      a.nnb + (long)m * n + i, dd, nullptr, a.status);
-        }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    const long gwarp = (long)blockIdx.x * wpb + warp, nwarps = (long)gridDim.x * wpb;
+    for (long it = gwarp; it < items; it += nwarps) {
+        const int m = a.order[it / n];
+        const int i = (int)(it % n);
+        real* dd = (real*)a.dedr + ((long)m * n + i) * NMAX * 3;
+        snap_atom_warp2<real, TJ>(sh.ws[warp], sh.tab, a.v.yt, sh.cg, sh.beff, a.v.sp, lane, n, i, a.q + m * a.stride,
+                                  a.qf + (long)m * n, box, a.nbr + ((long)m * n + i) * NMAX, a.nnb + (long)m * n + i,
+                                  dd, nullptr, a.status);
     }
 }
 
