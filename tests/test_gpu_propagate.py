@@ -175,3 +175,29 @@ def test_mistyped_step_counts_and_ids_are_rejected():
         with pytest.raises(TypeError):
             eng.baoab_propagate_batch(P.FINE, gq, gv, L, ids, lp)
     assert torch.equal(gq, T(q)) and torch.equal(gv, T(v))
+
+
+def _cluster(natoms, box_len, gen, dmin=2.3, spread=5.0):
+    pts = [np.full(3, box_len / 2)]
+    while len(pts) < natoms:
+        p = box_len / 2 + gen.uniform(-spread, spread, 3)
+        if all(np.linalg.norm(p - q) > dmin for q in pts):
+            pts.append(p)
+    return np.array(pts).T
+
+
+@pytest.mark.parametrize("natoms,nb", [(2, 2000), (17, 300)])
+def test_fp32_batches_spanning_many_members(natoms, nb):
+    """Tiny systems, many members: a batch of the FP32 kernel holds atoms of up to ~14 members and
+    a phase-B group of more; every member still matches the oracle."""
+    gen = W.rng(71, natoms)
+    box = np.full(3, 20.0)
+    base = _cluster(natoms, 20.0, gen)
+    q = np.ascontiguousarray(base[None] + gen.normal(0.0, 0.05, size=(nb, 3, natoms)))
+    v = W.velocities(natoms, 1000.0, W.rng(71, 100 + natoms), count=nb)
+    beta = W.fitted_beta()
+    L = W.rng(71, 200 + natoms).integers(0, 6, size=nb).astype(np.int32)
+    ids = np.arange(nb, dtype=np.int64)
+    gq, gv, oq, ov = _run_both(P.FINE, q, v, box, beta, L, ids, precision=P.FP32_BULK)
+    assert np.abs(gq - oq).max() < 1e-6
+    assert np.abs(gv - ov).max() < 1e-3
