@@ -275,7 +275,7 @@ int pmd_engine_reserve(pmd_engine* e, int nbatch) {
         (rc = e->s_dedr.ensure(na * PMD_MAX_NEIGHBORS * 3 * rs)) || (rc = e->s_qf.ensure(na * sizeof(float4))) ||
         (rc = e->s_vh.ensure(na * 3 * sizeof(double))) || (rc = e->s_order.ensure((2 * (size_t)nbatch + 4) * sizeof(int))) ||
         (rc = e->s_gstep.ensure(na * 3 * sizeof(double))) ||
-        (rc = e->s_flow.ensure((2 * (size_t)nbatch + 2) * sizeof(unsigned int))))
+        (rc = e->s_flow.ensure((2 * (size_t)nbatch + 2) * sizeof(unsigned long long))))
         return rc;
     if (e->p.natoms <= PMD_POS_TABLE_MAX_ATOMS && (rc = e->s_pos.ensure((size_t)na * e->p.natoms))) return rc;
     e->cap_batch = nbatch;

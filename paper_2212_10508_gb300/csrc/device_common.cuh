@@ -99,14 +99,16 @@ constexpr long long WAIT_POLLS = 20000000LL;
 
 // One thread: wait until *ctr >= target, at most `limit` polls.  The abort word ends the wait at
 // once (false); running out of polls sets the abort word and the status bit and returns false.
-__device__ __forceinline__ bool bounded_wait_geq(unsigned int* ctr, unsigned int target, unsigned int* abort_word,
-                                                 int* status, int timeout_bit, long long limit = WAIT_POLLS) {
-    cuda::atomic_ref<unsigned int, cuda::thread_scope_device> x(*ctr), ab(*abort_word);
+// U: unsigned int or unsigned long long words.
+template <typename U>
+__device__ __forceinline__ bool bounded_wait_geq(U* ctr, U target, U* abort_word, int* status, int timeout_bit,
+                                                 long long limit = WAIT_POLLS) {
+    cuda::atomic_ref<U, cuda::thread_scope_device> x(*ctr), ab(*abort_word);
     long long it = 0;
     while (x.load(cuda::memory_order_acquire) < target) {
         if (ab.load(cuda::memory_order_relaxed) != 0) return false;
         if (++it > limit) {
-            ab.store(1u, cuda::memory_order_relaxed);
+            ab.store(U(1), cuda::memory_order_relaxed);
             flag(status, timeout_bit);
             return false;
         }

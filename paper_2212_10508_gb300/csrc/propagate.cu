@@ -77,7 +77,8 @@ struct FineArgs {
     unsigned char* pos;     // reverse-slot tables [member][n][n], or nullptr (binary search)
     SBShape shape;          // FP32 path: run-time shape of the batched pass
     int b_group;            // atoms per warp in phase B (1..SB_B_GROUP_MAX)
-    unsigned int* flow;     // FP32 path: [0] next item, [1] abort, [2, 2 + nbatch) atoms done in phase A
+    unsigned long long* flow;   // FP32 path (64-bit words, no wrap for any launch): [0] next item, [1] abort,
+                                //   [2, 2 + nbatch) atoms done in phase A
                             // per member (order position), [2 + nbatch, 2 + 2 nbatch) in phase B
 };
 
@@ -337,7 +338,7 @@ __device__ __forceinline__ void flow_set(const FineArgs& a, FlowCursor& c, int b
 
 // Thread 0: wait until *ctr >= target (bounded; one item takes < 1 ms, the limit ~4 s; the abort
 // word ends every wait of the launch).
-__device__ __forceinline__ bool flow_wait(const FineArgs& a, unsigned int* ctr, unsigned int target) {
+__device__ __forceinline__ bool flow_wait(const FineArgs& a, unsigned long long* ctr, unsigned long long target) {
     return bounded_wait_geq(ctr, target, a.flow + 1, a.status, ST_TIMEOUT);
 }
 
@@ -346,7 +347,7 @@ __device__ __forceinline__ bool flow_wait(const FineArgs& a, unsigned int* ctr, 
 // path's barrier); both must give up after `polls` polls with ST_TIMEOUT.  words: [0] counter,
 // [1] abort word of the first wait, [2..5] barrier words.
 __global__ void k_selftest_waits(unsigned int* words, int* status, long long polls) {
-    if (threadIdx.x == 0) bounded_wait_geq(words, 1u, words + 1, status, ST_TIMEOUT, polls);
+    if (threadIdx.x == 0) bounded_wait_geq<unsigned int>(words, 1u, words + 1, status, ST_TIMEOUT, polls);
     __syncthreads();
     const GridBarrier gb{words + 2, 2u};
     grid_sync(gb, status, ST_TIMEOUT, polls);
@@ -369,14 +370,14 @@ __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
     const int nw = blockDim.x >> 5;
     const int bmax = nw * a.b_group;   // phase-B item: at most b_group atoms per warp
     const double box[3] = {a.box0, a.box1, a.box2};
-    unsigned int* doneA = a.flow + 2;
-    unsigned int* doneB = a.flow + 2 + a.nbatch;
+    unsigned long long* doneA = a.flow + 2;
+    unsigned long long* doneB = a.flow + 2 + a.nbatch;
     FlowCursor c;   // thread 0's view of the sequence (items are taken in increasing order)
     if (threadIdx.x == 0) flow_set(a, c, bmax);
     for (;;) {
         if (threadIdx.x == 0) {
-            cuda::atomic_ref<unsigned int, cuda::thread_scope_device> head(a.flow[0]), ab(a.flow[1]);
-            const long t = ab.load(cuda::memory_order_relaxed) != 0 ? -1 : (long)head.fetch_add(1u, cuda::memory_order_relaxed);
+            cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> head(a.flow[0]), ab(a.flow[1]);
+            const long t = ab.load(cuda::memory_order_relaxed) != 0 ? -1 : (long)head.fetch_add(1ull, cuda::memory_order_relaxed);
             while (t >= 0 && c.A > 0 && t >= c.base + c.nA + c.nB) {
                 c.base += c.nA + c.nB;
                 ++c.ell;
@@ -396,8 +397,8 @@ __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
             bool ok = true;
             if (ph >= 0 && !(ph == 0 && c.ell == 0)) {
                 for (long p = s / n; p <= (e - 1) / n && ok; ++p)
-                    ok = ph == 0 ? flow_wait(a, doneB + p, (unsigned int)((long)c.ell * n))
-                                 : flow_wait(a, doneA + p, (unsigned int)((long)(c.ell + 1) * n));
+                    ok = ph == 0 ? flow_wait(a, doneB + p, (unsigned long long)c.ell * n)
+                                 : flow_wait(a, doneA + p, (unsigned long long)(c.ell + 1) * n);
             }
             s_item[0] = c.ell;
             s_item[1] = ok ? ph : -1;
@@ -428,11 +429,11 @@ __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
             __syncthreads();
         }
         if (threadIdx.x == 0) {   // publish: the item's atoms per member
-            unsigned int* done = ph == 0 ? doneA : doneB;
+            unsigned long long* done = ph == 0 ? doneA : doneB;
             for (long p = s / n; p <= (e - 1) / n; ++p) {
                 const long lo = p * n > s ? p * n : s, hi = (p + 1) * n < e ? (p + 1) * n : e;
-                cuda::atomic_ref<unsigned int, cuda::thread_scope_device> x(done[p]);
-                x.fetch_add((unsigned int)(hi - lo), cuda::memory_order_release);
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> x(done[p]);
+                x.fetch_add((unsigned long long)(hi - lo), cuda::memory_order_release);
             }
         }
     }
@@ -488,9 +489,10 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
     unsigned int* words = reinterpret_cast<unsigned int*>(e->status.as<int>() + 1);
     a.bar = words;
     a.status = e->status.as<int>();
-    a.flow = e->s_flow.as<unsigned int>();
+    a.flow = e->s_flow.as<unsigned long long>();
     PMD_CUDA_TRY(cudaMemsetAsync(words, 0, 4 * sizeof(unsigned int), st));
-    if (sizeof(real) == 4) PMD_CUDA_TRY(cudaMemsetAsync(a.flow, 0, (2 * (size_t)nbatch + 2) * sizeof(unsigned int), st));
+    if (sizeof(real) == 4)
+        PMD_CUDA_TRY(cudaMemsetAsync(a.flow, 0, (2 * (size_t)nbatch + 2) * sizeof(unsigned long long), st));
     k_fine_prologue<<<1, 1024, 0, st>>>(nsteps, nbatch, lp.schedule, e->s_order.as<int>(), (int*)a.Ls, (int*)a.Lmax,
                                         a.status);
     PMD_CUDA_TRY(cudaGetLastError());
