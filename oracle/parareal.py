@@ -11,7 +11,7 @@ are batch callables ``F(states, ns) -> states`` and ``C(states, ns) -> states`` 
 ``ns`` are the interval indices n (interval [n dt, (n+1) dt], noise key n).  Nothing is
 cached: ``C(prev_n)`` is recomputed where Algorithm 2 asks for it.
 
-Readings of the paper used here (each also listed in the design doc):
+Readings of the paper used here:
   * |.| is the Euclidean norm of the 3m-vector of (unwrapped) positions;
   * metric "maxdisp" (for thresholds in Angstrom) replaces the relative error by the
     largest per-atom displacement |q_i^k - q_i^{k-1}| over the sub-window;

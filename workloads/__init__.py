@@ -5,7 +5,7 @@ supercell with a <111> dumbbell self-interstitial, the system of Sec. 3.1), seed
 random draws (thermal displacements, Maxwell-Boltzmann velocities, random SNAP
 coefficients, uneven interval lengths) and the workload definitions.
 
-Recipe (stated again in the design doc):
+Recipe:
   * lattice: n x n x n conventional BCC cells, a = 3.1652 Angstrom, periodic box n*a;
   * SIA: the atom at the site nearest the box centre is replaced by two atoms at
     s +- 1.1 Angstrom * (1,1,1)/sqrt(3)  (2 n^3 + 1 atoms);
