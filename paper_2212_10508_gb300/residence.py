@@ -10,7 +10,8 @@ alone from the sequential trajectory's state.  Window w draws its noise with see
 ids 0 .. window - 1 on both sides, so the two trajectories share every Gaussian increment and
 differ only through the parareal tolerance.  The interstitial's well in every
 frame comes from sia_locate (Wigner-Seitz reading of the Voronoi analysis), the residence times
-from sia_residence.  Prints one JSON line.
+from sia_residence.  Prints one JSON line.  Run it from the repository root: the seeded inputs
+(lattice, fitted coefficients, velocities) come from the `workloads` module there.
 """
 import argparse
 import json
