@@ -235,8 +235,11 @@ int pmd_engine_autotune(pmd_engine* e, int nbatch, int natoms, const double* q, 
  *                 [nbatch][3][natoms] arrays, 6*natoms to work inside packed states)
  *   nsteps        [nbatch] int32 device, 0 <= nsteps[b]
  *   interval_id   [nbatch] int64 device
- * FINE runs as one persistent cooperative kernel over all members (per-step grid barriers
- * with bounded waits: ETIMEOUT if a wait gives up); COARSE runs one CTA per member.
+ * FINE runs as one persistent cooperative kernel over all members: FP32_BULK as a dataflow
+ * schedule (each member's sub-steps wait only on that member's own work), FP64 with per-step
+ * grid barriers; every wait is bounded (ETIMEOUT at pmd_sync_status if one gives up).  The
+ * results do not depend on the batch composition: a member gives the same bits alone or in any
+ * batch.  COARSE runs one CTA per member.
  * natoms must equal the engine's natoms.  Stream-ordered. */
 int baoab_propagate_batch(pmd_engine* e, int potential, int nbatch, int natoms, double* q, double* v,
                           int64_t member_stride, const int32_t* nsteps, const int64_t* interval_id,
