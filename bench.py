@@ -38,7 +38,7 @@ SMALL = "profiling case: the same 64 intervals with L_b ~ U{5..20}"
 # capture of this workload (profiles/fine_persistent_batch64_dram.md), valid only for the kernel
 # sources it was taken on (fingerprint of the persistent kernel's translation unit and of the host
 # code that builds its tables); reported as null otherwise.
-TRAFFIC = {"bytes_per_launch": 3.47e6 + 45.87e6, "csrc_sha256_16": "c42b48648e4e8901"}
+TRAFFIC = {"bytes_per_launch": 3.47e6 + 45.87e6, "csrc_sha256_16": "cf52c70b9164b7bc"}
 
 
 KERNEL_SOURCES = ("propagate.cu", "snap.cu", "snap_kernels.cuh", "snap_batch.cuh", "snap_v2.cuh", "snap_device.cuh",

@@ -194,10 +194,10 @@ int pmd_sync_status(pmd_engine* e, pmd_stream_t stream);
 int pmd_engine_profile(pmd_engine* e, int enable, double* last_ms);
 
 /* Self-test of the bounded cross-CTA waits (failure detection without a GPU fault): launches one
- * CTA that waits on a counter nothing increments (the wait of the fine kernel's dataflow
- * schedule) and then on a two-CTA grid barrier with only itself launched (the barrier of the
- * FP64 path), each for at most `polls` polls (>= 1; ~200 ns each).  Both give up, and the next
- * pmd_sync_status returns PMD_ETIMEOUT; the engine stays usable.  EINVAL for polls < 1. */
+ * CTA that waits on counters nothing increments (64-bit, as in the fine kernel's dataflow
+ * schedule, and 32-bit) and then on a two-CTA grid barrier with only itself launched (the barrier
+ * of the FP64 path), each for at most `polls` polls (>= 1; ~200 ns each).  All give up, and the
+ * next pmd_sync_status returns PMD_ETIMEOUT; the engine stays usable.  EINVAL for polls < 1. */
 int pmd_engine_selftest_waits(pmd_engine* e, long long polls, pmd_stream_t stream);
 
 /* Run-time shape of the batched FP32 fine kernel (the FP64 form ignores it):

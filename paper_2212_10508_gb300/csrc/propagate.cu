@@ -342,23 +342,28 @@ __device__ __forceinline__ bool flow_wait(const FineArgs& a, unsigned long long*
     return bounded_wait_geq(ctr, target, a.flow + 1, a.status, ST_TIMEOUT);
 }
 
-// Self-test of the bounded waits: one CTA waits on a counter that nothing increments (the
-// scheduler's wait) and then on a grid barrier of two CTAs with only itself launched (the FP64
-// path's barrier); both must give up after `polls` polls with ST_TIMEOUT.  words: [0] counter,
-// [1] abort word of the first wait, [2..5] barrier words.
-__global__ void k_selftest_waits(unsigned int* words, int* status, long long polls) {
-    if (threadIdx.x == 0) bounded_wait_geq<unsigned int>(words, 1u, words + 1, status, ST_TIMEOUT, polls);
+// Self-test of the bounded waits: one CTA waits on a 64-bit counter that nothing increments (the
+// dataflow schedule's wait), then on a 32-bit one, then on a grid barrier of two CTAs with only
+// itself launched (the FP64 path's barrier); each must give up after `polls` polls with
+// ST_TIMEOUT.  w64: [0] counter, [1] abort word; w32: [0] counter, [1] abort word, [2..5]
+// barrier words.
+__global__ void k_selftest_waits(unsigned long long* w64, unsigned int* w32, int* status, long long polls) {
+    if (threadIdx.x == 0) {
+        bounded_wait_geq<unsigned long long>(w64, 1ull, w64 + 1, status, ST_TIMEOUT, polls);
+        bounded_wait_geq<unsigned int>(w32, 1u, w32 + 1, status, ST_TIMEOUT, polls);
+    }
     __syncthreads();
-    const GridBarrier gb{words + 2, 2u};
+    const GridBarrier gb{w32 + 2, 2u};
     grid_sync(gb, status, ST_TIMEOUT, polls);
 }
 
 int selftest_waits(pmd_engine* e, long long polls, cudaStream_t st) {
     int rc;
-    if ((rc = e->s_selftest.ensure(8 * sizeof(unsigned int)))) return rc;
-    unsigned int* w = e->s_selftest.as<unsigned int>();
-    PMD_CUDA_TRY(cudaMemsetAsync(w, 0, 8 * sizeof(unsigned int), st));
-    k_selftest_waits<<<1, 32, 0, st>>>(w, e->status.as<int>(), polls);
+    if ((rc = e->s_selftest.ensure(8 * sizeof(unsigned long long)))) return rc;
+    unsigned long long* w64 = e->s_selftest.as<unsigned long long>();   // [0, 2): 64-bit words
+    unsigned int* w32 = reinterpret_cast<unsigned int*>(w64 + 2);        // [2, 8): 32-bit words
+    PMD_CUDA_TRY(cudaMemsetAsync(w64, 0, 8 * sizeof(unsigned long long), st));
+    k_selftest_waits<<<1, 32, 0, st>>>(w64, w32, e->status.as<int>(), polls);
     PMD_CUDA_TRY(cudaGetLastError());
     return PMD_OK;
 }
