@@ -149,13 +149,16 @@ int pmd_snap_sync_status(pmd_snap* s, pmd_stream_t stream);
  * allocate device memory while they run (an application that owns all device memory through
  * its own allocator, a loop where cudaMalloc would stall or is not allowed, a fixed memory
  * budget).  The paper has no counterpart; it is an interface addition of this library.
- * Scratch comes from one array of PMD_NOALLOC_SCRATCH_BYTES compiled into the library and
- * resident on every device that loads it; the call allocates nothing.  The context s must
- * exist already (its tables are allocated by pmd_snap_create).  The first call on a device
- * looks up that device's address of the array (make it before any stream capture).  All
- * calls on a device share the array: calls whose kernels overlap on the GPU race on it.
- * Requests whose scratch exceeds the array (about 1 KiB per atom for FP32 forces, 3.7 KiB
- * with energies; twice that in FP64) return PMD_EUNSUPPORTED. */
+ * Scratch comes from one array of PMD_NOALLOC_SCRATCH_BYTES compiled into the library.
+ * pmd_snap_create loads that array on its device (with lazy module loading, the CUDA default,
+ * this is when its 16 MiB are reserved), and the device keeps it until the process exits; the
+ * call itself allocates nothing.  The context s must exist already (its tables are allocated
+ * by pmd_snap_create) and must belong to the current device.  Each call looks up the array's
+ * address in the current context.  All calls on a device share the array and find the last
+ * call's contents there: calls whose kernels overlap on the GPU race on it.  Box and argument
+ * checks are those of snap_energy_forces.  Requests whose scratch exceeds the array (about
+ * 1 KiB per atom for FP32 forces, 3.7 KiB with energies; twice that in FP64) return
+ * PMD_EUNSUPPORTED. */
 #define PMD_NOALLOC_SCRATCH_BYTES (16u << 20)
 int snap_energy_forces_noalloc(pmd_snap* s, int nbatch, int natoms, const double box[3], const double* pos,
                                const double* beta, double* energy, double* forces, double* sumB,

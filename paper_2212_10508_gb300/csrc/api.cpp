@@ -88,7 +88,7 @@ static int check_fs(const pmd_fs_params* p) {
     return PMD_OK;
 }
 
-static int check_box(const double box[3], double rc) {
+int check_box(const double box[3], double rc) {
     if (!box) return fail(PMD_EINVAL, "box is NULL");
     for (int a = 0; a < 3; ++a)
         if (!(box[a] > 2.0 * rc) || !std::isfinite(box[a]))
@@ -118,6 +118,7 @@ static int read_status(int* dstatus, cudaStream_t st) {
 }
 
 int selftest_waits(pmd_engine* e, long long polls, cudaStream_t st);
+int noalloc_scratch_address(void** out);
 }  // namespace pmd
 
 using namespace pmd;
@@ -135,7 +136,12 @@ int pmd_snap_create(const pmd_snap_params* p, pmd_snap** out) {
     if (!s) return fail(PMD_ENOMEM, "pmd_snap_create: out of host memory");
     s->p = *p;
     cudaGetDevice(&s->device);
-    if ((rc = build_snap_tables(p->twojmax, &s->T)) || (rc = snap_upload(s)) || (rc = s->s_status.ensure(sizeof(int)))) {
+    // noalloc_scratch_address also loads the module that holds the static scratch array of
+    // snap_energy_forces_noalloc, so that its device memory is reserved here (where allocating
+    // is allowed) and not by the first allocation-free call.
+    void* noalloc_base = nullptr;
+    if ((rc = build_snap_tables(p->twojmax, &s->T)) || (rc = snap_upload(s)) || (rc = s->s_status.ensure(sizeof(int))) ||
+        (rc = noalloc_scratch_address(&noalloc_base))) {
         pmd_snap_destroy(s);
         return rc;
     }

@@ -25,6 +25,9 @@ int cuda_fail(cudaError_t err, const char* what);
 
 int status_to_code(int bits);
 
+// PMD_OK if every box edge is finite and exceeds 2 rc, else PMD_EINVAL with a message.
+int check_box(const double box[3], double rc);
+
 // ---- device buffers --------------------------------------------------------------------
 struct DevBuf {
     void* p = nullptr;

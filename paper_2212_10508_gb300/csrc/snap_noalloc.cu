@@ -8,15 +8,16 @@
 // cudaMalloc on the first call of a new size; this variant takes its scratch from one
 // fixed-size array compiled into the library instead.
 //
-// The array below lives in every GPU that loads the library, for the life of the process
-// (PMD_NOALLOC_SCRATCH_BYTES = 16 MiB).  Host code cannot use the array's name as a device
-// address, so the address is looked up once per device with cudaGetSymbolAddress, on the
-// first call made with that device current; make that first call before any stream capture.
-// Every call on a device shares the array and leaves its contents behind: two calls whose
-// kernels overlap on the GPU (different streams without ordering) race on it.  No part of the
-// scratch has to start at zero: the kernels write every entry they later read.
-#include <mutex>
-
+// The array below (PMD_NOALLOC_SCRATCH_BYTES = 16 MiB) belongs to this file's CUDA module.
+// With lazy module loading (the CUDA default) a module's memory is reserved when the module
+// is first used on a device, so pmd_snap_create loads it on its device by asking for the
+// array's address; from then on the device holds the array until the process exits and the
+// entry point itself allocates nothing.  Host code cannot use the array's name as a device
+// address: every call asks the runtime for the address in the current context (cheap once the
+// module is loaded, and never stale after the context is re-created).  Every call on a device
+// shares the array and leaves its contents behind: two calls whose kernels overlap on the GPU
+// (different streams without ordering) race on it.  No part of the scratch has to start at
+// zero: the kernels write every entry they later read.
 #include "pmd_internal.h"
 
 namespace pmd {
@@ -27,21 +28,13 @@ int snap_compute_scratch(pmd_snap* s, int nbatch, int n, const double box[3], co
 
 static __device__ __align__(256) unsigned char g_snap_noalloc_scratch[PMD_NOALLOC_SCRATCH_BYTES];
 
-static std::mutex g_noalloc_mutex;
-static void* g_noalloc_addr[256];   // per device ordinal; filled by the first call on that device
-
-static int noalloc_base(void** out) {
-    int dev = 0;
-    PMD_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 256) return fail(PMD_EUNSUPPORTED, "snap_energy_forces_noalloc: device ordinal >= 256");
-    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_snap_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-        g_noalloc_addr[dev] = p;
-    }
-    *out = g_noalloc_addr[dev];
+// Device address of the scratch array in the current context; the first request on a device
+// loads this module there (pmd_snap_create makes that request).
+int noalloc_scratch_address(void** out) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_snap_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+    *out = p;
     return PMD_OK;
 }
 
@@ -54,9 +47,8 @@ extern "C" int snap_energy_forces_noalloc(pmd_snap* s, int nbatch, int natoms, c
                                           double* sumB, pmd_stream_t stream) {
     if (!s) return fail(PMD_EINVAL, "snap_energy_forces_noalloc: NULL context");
     if (nbatch < 0 || natoms < 1) return fail(PMD_EINVAL, "snap_energy_forces_noalloc: need nbatch >= 0, natoms >= 1");
-    if (!box) return fail(PMD_EINVAL, "snap_energy_forces_noalloc: box is NULL");
-    for (int a = 0; a < 3; ++a)
-        if (!(box[a] > 2.0 * s->p.rcut)) return fail(PMD_EINVAL, "snap_energy_forces_noalloc: box edge <= 2 rcut");
+    int rc = check_box(box, s->p.rcut);
+    if (rc) return rc;
     if (nbatch == 0) return PMD_OK;
     if (!pos || !beta) return fail(PMD_EINVAL, "snap_energy_forces_noalloc: pos and beta are required");
     const long na = (long)nbatch * natoms;
@@ -72,8 +64,7 @@ extern "C" int snap_energy_forces_noalloc(pmd_snap* s, int nbatch, int natoms, c
                                           " needs " + std::to_string(total) + " bytes of scratch; the static array holds " +
                                           std::to_string((size_t)PMD_NOALLOC_SCRATCH_BYTES) + " bytes");
     void* base = nullptr;
-    int rc = noalloc_base(&base);
-    if (rc) return rc;
+    if ((rc = noalloc_scratch_address(&base))) return rc;
     unsigned char* b = static_cast<unsigned char*>(base);
     SnapScratch sc{reinterpret_cast<int*>(b + off[0]), reinterpret_cast<int*>(b + off[1]), b + off[2],
                    reinterpret_cast<float4*>(b + off[3]), sz[4] ? b + off[4] : nullptr,

@@ -114,3 +114,22 @@ def test_adaptive_restart_degenerate_explosion_at_slab_start(lib):
     assert (a.n_in, a.n_fin) == (1, 3)
     with pytest.raises(P.PmdError):
         st.adaptive_restart(1.0, 9)          # n_stop outside the slab
+
+
+def test_adaptive_restart_follows_the_hand_worked_trace(lib):
+    """The library's Algorithm 2 state machine fed the errors of the linear problem F x = x,
+    C x = 0.7 x (N = 8, delta_expl = 0.35, delta_conv = 0.05; errors from the closed form,
+    worked out by hand in tests/test_oracle_parareal.py) produces the hand-derived slabs and
+    the eq. (7) cost 8 C_f + 56 C_c."""
+    st = P.Adaptive(8, 0.05, 0.35)
+    act = st.adaptive_restart()
+    steps = [((0, 8), 0.4583, 2), ((0, 2), 0.0309, 2), ((2, 8), 0.4583, 4), ((2, 4), 0.0309, 4),
+             ((4, 8), 0.4583, 6), ((4, 6), 0.0309, 6), ((6, 8), 0.3288, 8), ((6, 8), 0.0309, 8)]
+    for (rng, delta, n_stop) in steps:
+        assert act.kind == P.ACT_ITERATE and (act.n_in, act.n_fin) == rng
+        act = st.adaptive_restart(delta, n_stop)
+    assert act.kind == P.ACT_DONE
+    assert st.log() == [(0, 8, 1, 0), (0, 2, 1, 0), (2, 8, 1, 1), (2, 4, 1, 1), (4, 8, 1, 2), (4, 6, 1, 2),
+                        (6, 8, 2, 3)]
+    cost, g, gi = st.cost(1.0, 0.01)
+    assert cost == pytest.approx(8.56, rel=1e-14) and gi == 1.0

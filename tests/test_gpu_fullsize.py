@@ -16,6 +16,7 @@ import oracle as O
 import paper_2212_10508_gb300 as P
 import workloads as W
 from gpu_util import N, T, rel_max, torch
+from test_gpu_propagate import fp32_trajectory_bounds
 
 pytestmark = pytest.mark.gpu
 
@@ -76,3 +77,31 @@ def test_2001_atom_cell_full_size():
     Tk = _kinetic_temperature(gv)
     assert 500.0 < Tk.mean() < 1050.0, Tk.mean()
     _forces_match_oracle(gq[:1], box, beta)
+
+
+@pytest.mark.parametrize("precision", [P.FP64, P.FP32_BULK])
+def test_2001_atom_cell_trajectory_matches_oracle(precision):
+    """Two members of the 2001-atom cell, 20 and 13 steps at 1000 K with the fitted SNAP, against
+    the oracle's trajectory: FP64 to 1e-8 Angstrom; FP32-bulk within the bounds implied by the
+    1e-5 force bar."""
+    pos, box = W.bcc_sia(10)
+    n = pos.shape[1]
+    q = W.displaced(pos, 0.05, W.rng(62, 1), count=2)
+    v = W.velocities(n, 1000.0, W.rng(62, 2), count=2)
+    beta = W.fitted_beta()
+    L = np.array([20, 13], np.int32)
+    ids = np.array([5, 77], np.int64)
+    eng = P.Engine(n, box, P.snap_params(precision=precision), P.fs_params(precision=precision), beta=T(beta))
+    lp = P.langevin(dt=1e-3, gamma=1.0, T=1000.0, scheme=P.SCHEME_PAPER, schedule=P.SCHED_ROBUST, seed=62)
+    gq, gv = T(q), T(v)
+    eng.baoab_propagate_batch(P.FINE, gq, gv, T(L, torch.int32), T(ids, torch.int64), lp)
+    eng.sync_status()
+    oq, ov = q.copy(), v.copy()
+    olp = O.langevin(dt=1e-3, gamma=1.0, T=1000.0, scheme=O.SCHEME_PAPER, schedule=O.SCHED_ROBUST, seed=62)
+    O.propagate(O.potential(O.POT_SNAP, beta=beta), oq, ov, box, L, ids, olp)
+    dq, dv = np.abs(N(gq) - oq).max(), np.abs(N(gv) - ov).max()
+    if precision == P.FP64:
+        assert dq < 1e-8 and dv < 1e-6
+    else:
+        bq, bv = fp32_trajectory_bounds(q[:1], box, beta, 20)
+        assert dq < bq and dv < bv

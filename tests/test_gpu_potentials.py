@@ -40,10 +40,11 @@ def test_snap_fp32_bulk_matches_oracle_129_atoms():
 
 
 @pytest.mark.parametrize("twojmax", [2, 4, 6])
-def test_snap_other_band_limits(twojmax):
+@pytest.mark.parametrize("precision,tol", [(P.FP64, 1e-10), (P.FP32_BULK, 1e-5)])
+def test_snap_other_band_limits(twojmax, precision, tol):
     P_, box, _ = W.small_system(nconf=3)
     beta = W.snap_beta(W.n_bispectrum(twojmax), W.rng(5, twojmax))
-    _compare_snap(P_, box, beta, twojmax, P.FP64, 1e-10)
+    _compare_snap(P_, box, beta, twojmax, precision, tol)
 
 
 def test_snap_2001_atoms():

@@ -97,6 +97,31 @@ def test_fine_fp32_bulk_tracks_fp64():
     assert np.abs(gq - oq).max() < 1e-6
 
 
+def fp32_trajectory_bounds(q0, box, beta, nsteps, dt=1e-3, tol_f=1e-5, growth=2.0):
+    """Position and velocity bounds for an FP32-bulk trajectory against the FP64 oracle, from
+    the force bar alone: a force error |dF| <= tol_f max|F| (the FP32-bulk force tolerance,
+    max-norm relative), with max|F| allowed to grow by `growth` along the run, moves an atom by
+    at most (1/2) |dF|/m t^2 and changes its velocity by at most |dF|/m t after t = nsteps dt."""
+    _, F0, _ = O.snap_energy_forces(q0, box, beta)
+    a = tol_f * growth * np.abs(F0).max() * W.FTOA / W.M_W          # Angstrom / ps^2
+    t = nsteps * dt
+    return 0.5 * a * t * t, a * t
+
+
+def test_fine_fp32_bulk_100_step_trajectory():
+    """The 129-atom cell with the fitted SNAP, 100 FP32-bulk steps at 1500 K: positions and
+    velocities within the bounds that the 1e-5 force bar implies (1.2e-4 Angstrom here)."""
+    q, v, box, _ = _system(4, 2, 1500.0, 19)
+    beta = W.fitted_beta()
+    L = np.array([100, 100], dtype=np.int32)
+    ids = np.array([8, 9], dtype=np.int64)
+    gq, gv, oq, ov = _run_both(P.FINE, q, v, box, beta, L, ids, T_K=1500.0, precision=P.FP32_BULK)
+    bq, bv = fp32_trajectory_bounds(q[:1], box, beta, 100)
+    assert bq < 2e-4                     # max|F| = 22 eV/A at the dumbbell: bq = 1.2e-4 A
+    assert np.abs(gq - oq).max() < bq
+    assert np.abs(gv - ov).max() < bv
+
+
 def test_noise_is_shared_between_fine_and_coarse_zero_force():
     """With gamma > 0 and both potentials switched off (beta = 0 and FS A = pair = 0) the two
     propagators see the same G_{l,n}: their trajectories coincide exactly."""

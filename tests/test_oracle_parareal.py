@@ -109,6 +109,68 @@ def test_adaptive_windows_partition_and_converge():
     assert log.windows[-1]["subs"][-1][0] == N
 
 
+def _scalar_adaptive(delta_expl, delta_conv, N, metric="rel"):
+    trace = []
+    cur, log = PR.adaptive(np.array([1.0]), np.array([0.0]), N, delta_conv, delta_expl, _linear(1.0), _linear(0.7),
+                           metric=metric, trace=trace)
+    return cur, log, trace
+
+
+def test_adaptive_hand_worked_trace():
+    """Algorithm 2 on F x = x, C x = 0.7 x, N = 8, delta_expl = 0.35, delta_conv = 0.05.
+
+    Inside a slab that starts at N_init with value x_in, the k-th iterate m intervals later
+    is x^k_m = x_in sum_{j <= min(k, m)} binom(m, j) 0.3^j 0.7^(m-j) (the linear closed form
+    of test_classical_linear_closed_form, started at the slab), so the relative error
+    E(k, M) over the first M intervals of the slab does not depend on x_in or on which slab
+    it is:
+        k = 1:  M = 1: 0.1765   M = 2: 0.3288   M = 3: 0.4583
+        k = 2:  M = 1: 0        M = 2: 0.0309
+    Walking Algorithm 2 through this table by hand:
+      slab 1 (N_init = 0): k=1 on [0, 8] passes M = 1, 2 and fires at M = 3 (n = 2), so
+        N_final := n = 2; k=2 on [0, 2] ends with E(2, 2) = 0.0309 < delta_conv.
+      slabs 2 and 3 (N_init = 2, 4): the same, shortened to 4 and to 6.
+      slab 4 (N_init = 6): k=1 on [6, 8] ends with E(1, 2) = 0.3288, inside
+        [delta_conv, delta_expl], so a second iteration on the same end point follows, and
+        E(2, 2) = 0.0309 converges.
+    The log is therefore [(N_init, [(N_final^{i,j}, k^{i,j})])]:
+      (0, [(8, 1), (2, 1)]), (2, [(8, 1), (4, 1)]), (4, [(8, 1), (6, 1)]), (6, [(8, 2)]).
+    Every slab ends with k >= its length, so each slab's iterate is exact: x_n = 1."""
+    cur, log, trace = _scalar_adaptive(0.35, 0.05, 8)
+    got = [(w["n_init"], [tuple(s) for s in w["subs"]]) for w in log.windows]
+    assert got == [(0, [(8, 1), (2, 1)]), (2, [(8, 1), (4, 1)]), (4, [(8, 1), (6, 1)]), (6, [(8, 2)])]
+    # one trace record per iteration: (N_init, N_final before, delta, n_stop, N_final after)
+    assert [(t[0], t[1], t[3], t[4]) for t in trace] == [
+        (0, 8, 2, 2), (0, 2, 2, 2), (2, 8, 4, 4), (2, 4, 4, 4), (4, 8, 6, 6), (4, 6, 6, 6), (6, 8, 8, 8), (6, 8, 8, 8)]
+    assert [round(t[2], 4) for t in trace] == [0.4583, 0.0309, 0.4583, 0.0309, 0.4583, 0.0309, 0.3288, 0.0309]
+    for n in range(9):
+        assert cur[n][0][0] == pytest.approx(1.0, abs=1e-14)
+    assert log.k_conv() == [2, 2, 2, 2]
+    # eq. (7) on this log, term by term (C_f = 1, C_c = 0.01):
+    #   slab 1: 8 C_c + 1 (C_f + C_c + 8 C_c) + 1 (C_f + C_c + 2 C_c) = 2 C_f + 20 C_c
+    #   slab 2: 6 C_c + 1 (C_f + C_c + 6 C_c) + 1 (C_f + C_c + 2 C_c) = 2 C_f + 16 C_c
+    #   slab 3: 4 C_c + 1 (C_f + C_c + 4 C_c) + 1 (C_f + C_c + 2 C_c) = 2 C_f + 12 C_c
+    #   slab 4: 2 C_c + 2 (C_f + C_c + 2 C_c)                           = 2 C_f +  8 C_c
+    cost, g_adapt, g_ideal = PR.cost_and_gains(log, 8, 1.0, 0.01)
+    assert cost == pytest.approx(8.0 + 56 * 0.01, rel=1e-14)
+    assert g_adapt == pytest.approx(8.0 / 8.56, rel=1e-14)       # eq. (8)
+    assert g_ideal == 1.0                                          # eq. (9): 8 / (2 + 2 + 2 + 2)
+
+
+def test_adaptive_hand_worked_trace_with_empty_slab_clamp():
+    """Same problem with delta_expl = 0.15 < E(1, 1) = 0.1765: the first interval of every slab
+    already exceeds the threshold, so Algorithm 2's N_final := n would give N_final = N_init
+    (an empty slab, and no progress).  With the clamp N_final := N_init + 1 (the first
+    interval is exact after one iteration), each slab [n, n+1] is iterated once more and
+    converges with E = 0, except the last, where the clamp reaches N and the loop ends:
+      (0, [(4, 1), (1, 1)]), (1, [(4, 1), (2, 1)]), (2, [(4, 1), (3, 1)]), (3, [(4, 1)])."""
+    cur, log, _ = _scalar_adaptive(0.15, 0.05, 4)
+    got = [(w["n_init"], [tuple(s) for s in w["subs"]]) for w in log.windows]
+    assert got == [(0, [(4, 1), (1, 1)]), (1, [(4, 1), (2, 1)]), (2, [(4, 1), (3, 1)]), (3, [(4, 1)])]
+    for n in range(5):
+        assert cur[n][0][0] == pytest.approx(1.0, abs=1e-14)
+
+
 def test_cost_reduces_to_classical_formula():
     log = PR.AdaptiveLog()
     log.windows.append({"n_init": 0, "subs": [[100, 7]]})
