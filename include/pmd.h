@@ -131,6 +131,16 @@ int pmd_snap_reserve(pmd_snap* s, int nbatch, int natoms);
  * real fused multiply-add 2.  Used for roofline accounting; any pointer may be NULL. */
 int pmd_snap_flop_model(const pmd_snap* s, double* per_pair, double* per_atom);
 
+/* Measured FMA throughput of the current device, the denominator of the ALU roofline of the
+ * SNAP kernels (a microbenchmark; the paper has no counterpart).  kind: PMD_PEAK_FFMA (scalar
+ * FP32 fmaf), PMD_PEAK_FFMA2 (paired FP32 __ffma2_rn, the form the batched contraction uses) or
+ * PMD_PEAK_DFMA (FP64 fma).  Every SM is filled with 2048 threads running 16 (FP32) or 8 (FP64)
+ * independent FMA chains each; a short launch sizes one timed launch of about `seconds`
+ * (0 < seconds <= 10) on `stream`, timed with CUDA events.  *tflops = 2 x FMAs / time in
+ * TFLOP/s; *ms (may be NULL) the timed launch's duration.  Synchronises the stream. */
+enum { PMD_PEAK_FFMA = 0, PMD_PEAK_FFMA2 = 1, PMD_PEAK_DFMA = 2 };
+int pmd_alu_peak(int kind, double seconds, pmd_stream_t stream, double* tflops, double* ms);
+
 /* SNAP energies and forces of nbatch independent systems (Sec. 3.1).
  *   pos    [nbatch][3][natoms]  FP64 device, unwrapped Angstrom
  *   beta   [1+nB]               FP64 device, beta[0] = per-atom constant

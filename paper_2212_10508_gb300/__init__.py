@@ -82,7 +82,7 @@ EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_nu
            "pmd_engine_selftest_waits", "pmd_engine_get_tuning", "pmd_engine_set_tuning", "pmd_engine_autotune",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
            "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log", "sia_locate",
-           "sia_residence"]
+           "sia_residence", "pmd_alu_peak"]
 
 _lib = None
 
@@ -130,6 +130,7 @@ def lib():
     L.pmd_adaptive_log.argtypes = [vp, i32, ip, ip, ip, ip]
     L.sia_locate.argtypes = [i32, i32, i32, dp, vp, i64, vp, vp, vp, vp, vp]
     L.sia_residence.argtypes = [vp, i32, i32, vp, vp, ip]
+    L.pmd_alu_peak.argtypes = [i32, ctypes.c_double, vp, dp, dp]
     _lib = L
     return L
 
@@ -173,6 +174,16 @@ def fs_params(d=4.400224, A=1.896373, c=3.25, c0=47.1346499, c1=-33.7665655, c2=
 
 def langevin(dt=1e-3, gamma=1.0, T=1000.0, mass=183.84, scheme=SCHEME_PAPER, schedule=SCHED_ROBUST, seed=12345):
     return Langevin(dt, gamma, T, mass, scheme, schedule, seed & 0xFFFFFFFFFFFFFFFF)
+
+
+PEAK_FFMA, PEAK_FFMA2, PEAK_DFMA = 0, 1, 2
+
+
+def alu_peak(kind, seconds=0.2, stream=None):
+    """Measured FMA throughput of the current device in TFLOP/s (pmd_alu_peak)."""
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(lib().pmd_alu_peak(kind, seconds, _stream(stream), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value
 
 
 class Snap:

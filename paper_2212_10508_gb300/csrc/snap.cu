@@ -464,14 +464,16 @@ __global__ void __launch_bounds__(snap_cta_threads<real>(), 1)
 }
 
 // B_t of one atom from U_tot (full layout): Re sum_{m m'} conj(U^j) Z^j_{j1 j2}, FP64 accumulation.
+// Thread (t, atom), triple-major: the 32 lanes of a warp take 32 atoms of the same triple, so every
+// loop bound and Clebsch-Gordan index is warp-uniform.
 template <typename real, int TJ>
 __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, long natoms_all, int nB,
                                   const int4* __restrict__ triblk, const real* __restrict__ cg,
                                   const int4* __restrict__ blk, double* __restrict__ Bout) {
     const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= natoms_all * nB) return;
-    const long ia = idx / nB;
-    const int t = (int)(idx % nB);
+    const int t = (int)(idx / natoms_all);
+    const long ia = idx - (long)t * natoms_all;
     const int4 tb = triblk[t];
     const int ta = tb.y, tbb = tb.z, tj = tb.w;
     const int4 bk = blk[tb.x];
@@ -500,7 +502,7 @@ __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, long nato
             const cplx<real> u = Uj[p * (tj + 1) + q];
             B += (double)u.re * zr + (double)u.im * zi;
         }
-    Bout[idx] = B;
+    Bout[ia * nB + t] = B;
 }
 
 template <typename real>
@@ -518,30 +520,41 @@ __global__ void k_snap_gather(const int* __restrict__ nbr, const int* __restrict
     if (lane < 3) forces[bb * 3 * n + (long)lane * n + k] = F[lane == 0 ? 0 : (lane == 1 ? 1 : 2)];
 }
 
-// per member: E = sum_i (beta_0 + sum_t beta_t B_it), sumB[t] = sum_i B_it; fixed order.
-__global__ void k_snap_energy(const double* __restrict__ B, int nbatch, int n, int nB, const double* __restrict__ beta,
-                              double* __restrict__ energy, double* __restrict__ sumB) {
+// per member: E = sum_i (beta_0 + sum_t beta_t B_it), sumB[t] = sum_i B_it.  One CTA of
+// SNAP_E_THREADS per member: thread t sums column t of B over the atoms (sumB); for E every thread
+// sums the E_i of atoms i = thread, thread + SNAP_E_THREADS, ... and the partial sums are combined
+// by a fixed binary tree in shared memory.  Every sum runs in a fixed order: deterministic.
+constexpr int SNAP_E_THREADS = 128;
+
+__global__ void __launch_bounds__(SNAP_E_THREADS) k_snap_energy(const double* __restrict__ B, int nbatch, int n,
+                                                                 int nB, const double* __restrict__ beta,
+                                                                 double* __restrict__ energy,
+                                                                 double* __restrict__ sumB) {
+    __shared__ double part[SNAP_E_THREADS];
     const int bb = blockIdx.x;
     const double* Bm = B + (long)bb * n * nB;
-    for (int t = threadIdx.x; t < nB; t += blockDim.x) {
-        if (sumB) {
+    if (sumB) {
+        for (int t = threadIdx.x; t < nB; t += blockDim.x) {
             double s = 0.0;
             for (int i = 0; i < n; ++i) s += Bm[(long)i * nB + t];
             sumB[(long)bb * (1 + nB) + 1 + t] = s;
         }
+        if (threadIdx.x == 0) sumB[(long)bb * (1 + nB)] = (double)n;
     }
-    if (threadIdx.x == 0) {
-        if (sumB) sumB[(long)bb * (1 + nB)] = (double)n;
-        if (energy) {
-            double E = 0.0;
-            for (int i = 0; i < n; ++i) {
-                double Ei = beta[0];
-                for (int t = 0; t < nB; ++t) Ei += beta[1 + t] * Bm[(long)i * nB + t];
-                E += Ei;
-            }
-            energy[bb] = E;
-        }
+    if (!energy) return;
+    double e = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double Ei = beta[0];
+        for (int t = 0; t < nB; ++t) Ei += beta[1 + t] * Bm[(long)i * nB + t];
+        e += Ei;
     }
+    part[threadIdx.x] = e;
+    __syncthreads();
+    for (int w = SNAP_E_THREADS / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) part[threadIdx.x] += part[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) energy[bb] = part[0];
 }
 
 template <typename real, int TJ>
@@ -583,7 +596,7 @@ static int launch_snap(pmd_snap* s, int nbatch, int n, const double box[3], cons
             static_cast<const cplx<real>*>(sc.utot), na, s->T.nB, s->d_triblk.as<int4>(), s->d_cg.as<real>(),
             s->d_blk.as<int4>(), sc.B);
         PMD_CUDA_TRY(cudaGetLastError());
-        k_snap_energy<<<nbatch, 64, 0, st>>>(sc.B, nbatch, n, s->T.nB, beta, energy, sumB);
+        k_snap_energy<<<nbatch, SNAP_E_THREADS, 0, st>>>(sc.B, nbatch, n, s->T.nB, beta, energy, sumB);
         PMD_CUDA_TRY(cudaGetLastError());
     }
     return PMD_OK;

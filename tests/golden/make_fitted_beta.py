@@ -1,6 +1,6 @@
-"""Write tests/golden/beta_fs_w_2j8.txt: SNAP coefficients (2J = 8, 1 + 55 values) fitted by
-ridge regression (lambda = 1e-6) to Finnis-Sinclair tungsten energies and forces, computed with
-the FP64 oracle only.
+"""Write tests/golden/beta_fs_w_2j8.txt and beta_fs_w_2j6.txt: SNAP coefficients (2J = 8, 1 + 55
+values; 2J = 6, 1 + 30 values) fitted by ridge regression (lambda = 1e-6) to Finnis-Sinclair
+tungsten energies and forces, computed with the FP64 oracle only.
 
 Why: random coefficients beta_t ~ N(0, 0.01^2) give a SNAP without a repulsive core; the
 129-atom cell then collapses within ~150 steps at 1500 K.  The fitted coefficients give a stable
@@ -11,7 +11,13 @@ members each at 300, 800, 1500, 2200 and 3000 K, Langevin EAM dynamics (paper sc
 schedule, dt 2 fs, gamma 5/ps) sampled after 100, 200 and 300 steps: 60 configurations.
 Rows: energy per atom (weight 1) and every force component (weight 1).
 
-    python tests/golden/make_fitted_beta.py     (about 1-2 minutes on 8 cores)
+2J = 6 (config 4's recipe, small): workloads.fit_starts(master=6, groups=4, members=4) -- four
+temperatures drawn in 500-3000 K, each with four cells whose <111> dumbbell sits at a random
+site along a random <111> axis, 0.02 Angstrom displacements -- then the same Langevin EAM
+dynamics (dt 2 fs, gamma 5/ps, seed 1000 + group, interval ids 4 k + m) sampled after 100, 200
+and 300 steps: 48 configurations.
+
+    python tests/golden/make_fitted_beta.py     (about 2-3 minutes on 8 cores)
 """
 import os
 import sys
@@ -25,6 +31,7 @@ import oracle as O  # noqa: E402
 import workloads as W  # noqa: E402
 
 OUT = os.path.join(HERE, "beta_fs_w_2j8.txt")
+OUT6 = os.path.join(HERE, "beta_fs_w_2j6.txt")
 
 
 def training_set(master=4):
@@ -38,6 +45,19 @@ def training_set(master=4):
         lp = O.langevin(dt=2e-3, gamma=5.0, T=float(Tk), seed=1000 + it, schedule=O.SCHED_ROBUST)
         for k in range(3):
             O.propagate(fs, q, v, box, [100] * 4, [4 * k + m for m in range(4)], lp)
+            confs.extend(list(q.copy()))
+    return np.ascontiguousarray(np.array(confs)), box
+
+
+def training_set_cfg4(master=6, groups=4, members=4, snapshots=3):
+    starts, temps, box = W.fit_starts(master, groups, members)
+    fs = O.potential(O.POT_FS)
+    confs = []
+    for it, ((q0, v0), Tk) in enumerate(zip(starts, temps)):
+        q, v = q0.copy(), v0.copy()
+        lp = O.langevin(dt=2e-3, gamma=5.0, T=float(Tk), seed=1000 + it, schedule=O.SCHED_ROBUST)
+        for k in range(snapshots):
+            O.propagate(fs, q, v, box, [100] * members, [members * k + m for m in range(members)], lp)
             confs.extend(list(q.copy()))
     return np.ascontiguousarray(np.array(confs)), box
 
@@ -60,12 +80,21 @@ def fit(confs, box, lam=1e-6, twojmax=8):
     return np.linalg.solve(X.T @ X + lam * np.eye(1 + nt), X.T @ y)
 
 
-if __name__ == "__main__":
-    confs, box = training_set()
-    beta = fit(confs, box)
-    with open(OUT, "w") as fh:
-        fh.write("# SNAP 2J=8 coefficients beta_0..beta_55 fitted to Finnis-Sinclair W with the FP64 oracle\n")
+def write(path, beta, twojmax, nt):
+    with open(path, "w") as fh:
+        fh.write("# SNAP 2J=%d coefficients beta_0..beta_%d fitted to Finnis-Sinclair W with the FP64 oracle\n"
+                 % (twojmax, nt))
         fh.write("# written by tests/golden/make_fitted_beta.py (ridge lambda 1e-6; see its docstring)\n")
         for b in beta:
             fh.write("%.17g\n" % b)
-    print(OUT, beta[0], np.abs(beta[1:]).max())
+    print(path, beta[0], np.abs(beta[1:]).max())
+
+
+if __name__ == "__main__":
+    which = sys.argv[1:] or ["8", "6"]
+    if "8" in which:
+        confs, box = training_set()
+        write(OUT, fit(confs, box), 8, 55)
+    if "6" in which:
+        confs, box = training_set_cfg4()
+        write(OUT6, fit(confs, box, twojmax=6), 6, 30)

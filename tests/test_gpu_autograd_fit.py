@@ -50,3 +50,46 @@ def test_gpu_fit_reproduces_oracle_fit():
     beta = FIT.fit_beta_ridge(confs, box, E, F, lam=1e-6)
     gold = W.fitted_beta()
     assert rel_max(N(beta), gold) <= 1e-6
+
+
+def _cfg4_small():
+    """Config 4's recipe at the size of the oracle's 2J = 6 golden: 4 temperatures in 500-3000 K x 4
+    cells with a randomly placed <111> dumbbell x 3 snapshots = 48 configurations."""
+    confs, box = FIT.config4_set(6, groups=4, members=4, snapshots=3, device=dev())
+    E, F = FIT.fs_reference(confs, box)
+    return confs, box, E, F
+
+
+def test_gpu_fit_2j6_reproduces_oracle_fit():
+    """The FP64 ridge fit at 2J = 6 on config 4's recipe (random dumbbell placements, 500-3000 K),
+    training set generated and design built with the library, against the oracle's fit
+    (tests/golden/make_fitted_beta.py, beta_fs_w_2j6.txt)."""
+    confs, box, E, F = _cfg4_small()
+    beta = FIT.fit_beta_ridge(confs, box, E, F, lam=1e-6, twojmax=6)
+    assert rel_max(N(beta), W.fitted_beta(6)) <= 1e-6
+
+
+@pytest.mark.parametrize("twojmax", [6, 8])
+def test_fitted_forces_equal_central_differences_h1e5(twojmax):
+    """dE/dr of the fitted FP64 SNAP against central differences with h = 1e-5 Angstrom on 12
+    sampled coordinates of config 4's configurations (truncation ~h^2 E''' and roundoff
+    ~eps |E| / h are both ~1e-8 eV/Angstrom here)."""
+    confs, box, _, _ = _cfg4_small()
+    g = np.random.default_rng(twojmax)
+    coords = [(int(g.integers(confs.shape[0])), int(g.integers(3)), int(g.integers(confs.shape[2]))) for _ in range(12)]
+    err, rows = FIT.fd_check(T(W.fitted_beta(twojmax)), confs, box, coords, h=1e-5, twojmax=twojmax)
+    assert err < 1e-6, rows
+
+
+def test_fp32_bulk_fit_matches_fp64_fit():
+    """The same fit built from FP32-bulk design rows: its force and energy errors against
+    Finnis-Sinclair stay within 1 % of the FP64 fit's (the FP32-bulk rows differ from the FP64
+    rows by ~1e-6 relative)."""
+    confs, box, E, F = _cfg4_small()
+    out = {}
+    for prec in (P.FP64, P.FP32_BULK):
+        beta = FIT.fit_beta_ridge(confs, box, E, F, lam=1e-6, twojmax=6, precision=prec)
+        out[prec] = FIT.rmse(beta, confs, box, E, F, twojmax=6, precision=prec)
+    (e64, f64), (e32, f32) = out[P.FP64], out[P.FP32_BULK]
+    assert f32 <= 1.01 * f64 and e32 <= 1.01 * e64 + 1e-5
+    assert f64 < 0.5                                   # a usable fit: force RMSE well below typical forces

@@ -70,6 +70,41 @@ def bcc_sia(ncell: int, a: float = A_W, split: float = 1.1):
     return np.ascontiguousarray(out), box
 
 
+def bcc_sia_at(ncell: int, site: int, axis, a: float = A_W, split: float = 1.1):
+    """BCC supercell with the <111> dumbbell at lattice site `site` (an index of bcc()) along
+    axis (+-1, +-1, +-1): the site's atom is replaced by two atoms at s +- split * axis/sqrt(3)."""
+    pos, box = bcc(ncell, a)
+    u = np.asarray(axis, dtype=np.float64) / np.sqrt(3.0)
+    x = pos[:, site].copy()
+    rest = np.delete(pos, site, axis=1)
+    out = np.concatenate([rest, (x + split * u)[:, None], (x - split * u)[:, None]], axis=1)
+    return np.ascontiguousarray(out), box
+
+
+def fit_starts(master: int, groups: int, members: int, ncell: int = 4, tmin: float = 500.0,
+               tmax: float = 3000.0, sigma: float = 0.02):
+    """Starting states of the beta-fitting training set (config 4): `groups` temperatures drawn
+    uniformly in [tmin, tmax] K, each with `members` cells whose <111> dumbbell sits at a random
+    lattice site along a random one of the four <111> axes (random sign), with N(0, sigma^2)
+    displacements and Maxwell-Boltzmann velocities at the group's temperature.
+    Returns (list of (q [members,3,n], v [members,3,n]) per group, temperatures [groups], box)."""
+    g = rng(master, 31)
+    temps = g.uniform(tmin, tmax, size=groups)
+    nsite = 2 * ncell ** 3
+    starts = []
+    box = None
+    for k in range(groups):
+        qs = []
+        for m in range(members):
+            axis = g.choice([-1.0, 1.0], size=3)
+            cell, box = bcc_sia_at(ncell, int(g.integers(nsite)), axis)
+            qs.append(cell)
+        q = np.ascontiguousarray(np.array(qs) + rng(master, 1000 + k).normal(0.0, sigma, size=(members,) + qs[0].shape))
+        v = velocities(qs[0].shape[1], temps[k], rng(master, 2000 + k), count=members)
+        starts.append((q, v))
+    return starts, temps, box
+
+
 def displaced(pos, sigma, gen: np.random.Generator, count=None):
     """count copies (or one if None) of pos with i.i.d. Gaussian displacements."""
     if count is None:
@@ -96,9 +131,11 @@ def snap_beta(nB, gen: np.random.Generator, std=0.01, beta0=BETA0):
 GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "tests", "golden")
 
 
-def fitted_beta():
-    """SNAP 2J=8 coefficients (1 + 55) fitted to Finnis-Sinclair W (see tests/golden/make_fitted_beta.py)."""
-    vals = [float(ln) for ln in open(os.path.join(GOLDEN, "beta_fs_w_2j8.txt")) if ln.strip() and ln[0] != "#"]
+def fitted_beta(twojmax: int = 8):
+    """SNAP coefficients (1 + nB) fitted to Finnis-Sinclair W by the oracle: 2J = 8 (the bench's
+    potential) or 2J = 6 (config 4's recipe); see tests/golden/make_fitted_beta.py."""
+    name = {8: "beta_fs_w_2j8.txt", 6: "beta_fs_w_2j6.txt"}[twojmax]
+    vals = [float(ln) for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and ln[0] != "#"]
     return np.array(vals)
 
 
