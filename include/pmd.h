@@ -185,17 +185,28 @@ int eam_energy_forces(const pmd_fs_params* p, int nbatch, int natoms, const doub
  * ---------------------------------------------------------------------------------- */
 typedef struct pmd_engine pmd_engine;
 
+/* Coarse potential of an engine: Finnis-Sinclair EAM (Strategy II of Sec. 3, the default), or
+ * SNAP with 2J = 2 (SNAP-6, Strategy I of Sec. 3; coefficients set by pmd_engine_set_coarse_beta). */
+enum { PMD_COARSE_FS = 0, PMD_COARSE_SNAP = 1 };
+
 typedef struct {
     pmd_snap_params fine;   /* fine potential V_F */
-    pmd_fs_params coarse;   /* coarse potential V_C */
+    pmd_fs_params coarse;   /* coarse potential V_C when coarse_kind = PMD_COARSE_FS */
     double box[3];          /* Angstrom */
     int natoms;             /* atoms per system */
+    int coarse_kind;        /* PMD_COARSE_FS (0) or PMD_COARSE_SNAP */
+    pmd_snap_params coarse_snap;   /* V_C when coarse_kind = PMD_COARSE_SNAP: twojmax must be 2,
+                                      natoms <= 512 (EUNSUPPORTED otherwise) */
 } pmd_engine_params;
 
 int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out);
 int pmd_engine_destroy(pmd_engine* e);
 /* Copy the SNAP coefficients beta [1+nB] (device pointer) into the engine (stream-ordered). */
 int pmd_engine_set_beta(pmd_engine* e, const double* beta, pmd_stream_t stream);
+/* Copy the coefficients beta [1 + 5] (device pointer, beta[0] = beta_0) of a SNAP coarse
+ * potential (PMD_COARSE_SNAP) into the engine (stream-ordered); EINVAL for an EAM coarse
+ * potential.  They start at zero. */
+int pmd_engine_set_coarse_beta(pmd_engine* e, const double* beta, pmd_stream_t stream);
 /* Grow the engine's scratch for batches of up to nbatch systems. */
 int pmd_engine_reserve(pmd_engine* e, int nbatch);
 /* Synchronises the stream and returns (and clears) the engine's device status. */

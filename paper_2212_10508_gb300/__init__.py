@@ -56,9 +56,12 @@ class Langevin(ctypes.Structure):
                 ("seed", ctypes.c_uint64)]
 
 
+COARSE_FS, COARSE_SNAP = 0, 1
+
+
 class EngineParams(ctypes.Structure):
     _fields_ = [("fine", SnapParams), ("coarse", FSParams), ("box", ctypes.c_double * 3),
-                ("natoms", ctypes.c_int)]
+                ("natoms", ctypes.c_int), ("coarse_kind", ctypes.c_int), ("coarse_snap", SnapParams)]
 
 
 class FineTuning(ctypes.Structure):
@@ -82,7 +85,7 @@ EXPORTS = ["pmd_last_error", "pmd_snap_create", "pmd_snap_destroy", "pmd_snap_nu
            "pmd_engine_selftest_waits", "pmd_engine_get_tuning", "pmd_engine_set_tuning", "pmd_engine_autotune",
            "baoab_propagate_batch", "parareal_jumps", "parareal_correct", "pmd_adaptive_create",
            "pmd_adaptive_destroy", "adaptive_restart", "pmd_adaptive_cost", "pmd_adaptive_log", "sia_locate",
-           "sia_residence", "pmd_alu_peak"]
+           "sia_residence", "pmd_alu_peak", "pmd_engine_set_coarse_beta"]
 
 _lib = None
 
@@ -131,6 +134,7 @@ def lib():
     L.sia_locate.argtypes = [i32, i32, i32, dp, vp, i64, vp, vp, vp, vp, vp]
     L.sia_residence.argtypes = [vp, i32, i32, vp, vp, ip]
     L.pmd_alu_peak.argtypes = [i32, ctypes.c_double, vp, dp, dp]
+    L.pmd_engine_set_coarse_beta.argtypes = [vp, vp, vp]
     _lib = L
     return L
 
@@ -272,11 +276,15 @@ def eam_energy_forces(pos, box, params: FSParams = None, energy=True, forces=Tru
 
 
 class Engine:
-    """Fine (SNAP) + coarse (EAM) potentials on one periodic cell of ``natoms`` atoms."""
+    """Fine (SNAP) + coarse potentials on one periodic cell of ``natoms`` atoms.  The coarse
+    potential is Finnis-Sinclair EAM (``coarse``), or SNAP with 2J = 2 when ``coarse_snap``
+    (SnapParams) is given, with coefficients ``coarse_beta`` (Strategy I of the paper)."""
 
-    def __init__(self, natoms, box, fine: SnapParams = None, coarse: FSParams = None, beta=None):
+    def __init__(self, natoms, box, fine: SnapParams = None, coarse: FSParams = None, beta=None,
+                 coarse_snap: SnapParams = None, coarse_beta=None):
+        kind = COARSE_SNAP if coarse_snap is not None else COARSE_FS
         self.params = EngineParams(fine or snap_params(), coarse or fs_params(), (ctypes.c_double * 3)(*box),
-                                   natoms)
+                                   natoms, kind, coarse_snap or snap_params(twojmax=2))
         h = ctypes.c_void_p()
         _check(lib().pmd_engine_create(ctypes.byref(self.params), ctypes.byref(h)))
         self.h = h
@@ -284,6 +292,11 @@ class Engine:
         self.box = tuple(float(x) for x in box)
         if beta is not None:
             self.set_beta(beta)
+        if coarse_beta is not None:
+            self.set_coarse_beta(coarse_beta)
+
+    def set_coarse_beta(self, beta, stream=None):
+        _check(lib().pmd_engine_set_coarse_beta(self.h, _ptr(beta), _stream(stream)))
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:

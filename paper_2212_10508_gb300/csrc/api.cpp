@@ -222,10 +222,16 @@ int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out) {
     *out = nullptr;
     if (!p) return fail(PMD_EINVAL, "pmd_engine_create: params are NULL");
     int rc;
-    if ((rc = check_snap_params(&p->fine)) || (rc = check_fs(&p->coarse))) return rc;
+    const bool csnap = p->coarse_kind == PMD_COARSE_SNAP;
+    if (p->coarse_kind != PMD_COARSE_FS && !csnap) return fail(PMD_EINVAL, "pmd_engine_create: bad coarse_kind");
+    if ((rc = check_snap_params(&p->fine)) || (rc = csnap ? check_snap_params(&p->coarse_snap) : check_fs(&p->coarse)))
+        return rc;
     if (p->natoms < 1 || p->natoms > PMD_MAX_COARSE_ATOMS)
         return fail(PMD_EUNSUPPORTED, "pmd_engine_create: natoms must be in 1..PMD_MAX_COARSE_ATOMS");
-    if ((rc = check_box(p->box, std::fmax(p->fine.rcut, std::fmax(p->coarse.d, p->coarse.c))))) return rc;
+    if (csnap && (p->coarse_snap.twojmax != 2 || p->natoms > 512))
+        return fail(PMD_EUNSUPPORTED, "pmd_engine_create: a SNAP coarse potential needs twojmax = 2 and natoms <= 512");
+    const double rc_coarse = csnap ? p->coarse_snap.rcut : std::fmax(p->coarse.d, p->coarse.c);
+    if ((rc = check_box(p->box, std::fmax(p->fine.rcut, rc_coarse)))) return rc;
     pmd_engine* e = new (std::nothrow) pmd_engine();
     if (!e) return fail(PMD_ENOMEM, "pmd_engine_create: out of host memory");
     e->p = *p;
@@ -234,6 +240,18 @@ int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out) {
     if ((rc = pmd_snap_create(&p->fine, &e->snap))) {
         delete e;
         return rc;
+    }
+    if (csnap) {
+        if ((rc = pmd_snap_create(&p->coarse_snap, &e->csnap)) ||
+            (rc = e->cbeta.ensure((size_t)(1 + e->csnap->T.nB) * sizeof(double)))) {
+            pmd_engine_destroy(e);
+            return rc;
+        }
+        cudaError_t ce0 = cudaMemset(e->cbeta.p, 0, e->cbeta.bytes);
+        if (ce0 != cudaSuccess) {
+            pmd_engine_destroy(e);
+            return cuda_fail(ce0, "pmd_engine_create");
+        }
     }
     if ((rc = e->beta.ensure((size_t)(1 + e->snap->T.nB) * sizeof(double))) ||
         (rc = e->status.ensure(16 * sizeof(int))) || (rc = e->s_result.ensure(64))) {
@@ -255,13 +273,21 @@ int pmd_engine_destroy(pmd_engine* e) {
     if (!e) return PMD_OK;
     DevBuf* bufs[] = {&e->beta, &e->status, &e->s_nbr, &e->s_nnb, &e->s_dedr, &e->s_qf, &e->s_vh, &e->s_order,
                       &e->s_result, &e->s_noise, &e->s_gstep, &e->s_pos, &e->s_flow,
-                      &e->s_selftest};
+                      &e->s_selftest, &e->cbeta};
     for (DevBuf* b : bufs) b->release();
     if (e->pinned) cudaFreeHost(e->pinned);
     if (e->ev0) cudaEventDestroy(e->ev0);
     if (e->ev1) cudaEventDestroy(e->ev1);
     pmd_snap_destroy(e->snap);
+    pmd_snap_destroy(e->csnap);
     delete e;
+    return PMD_OK;
+}
+
+int pmd_engine_set_coarse_beta(pmd_engine* e, const double* beta, pmd_stream_t stream) {
+    if (!e || !beta) return fail(PMD_EINVAL, "pmd_engine_set_coarse_beta: NULL argument");
+    if (!e->csnap) return fail(PMD_EINVAL, "pmd_engine_set_coarse_beta: the engine's coarse potential is not SNAP");
+    PMD_CUDA_TRY(cudaMemcpyAsync(e->cbeta.p, beta, e->cbeta.bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
     return PMD_OK;
 }
 

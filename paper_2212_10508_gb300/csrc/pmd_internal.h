@@ -116,6 +116,8 @@ struct pmd_engine {
     pmd_engine_params p;
     pmd_snap* snap = nullptr;        // owned
     pmd::DevBuf beta;                // [1+nB] FP64
+    pmd_snap* csnap = nullptr;       // SNAP coarse potential (PMD_COARSE_SNAP), owned
+    pmd::DevBuf cbeta;               // its coefficients [1+nB] FP64
     pmd::DevBuf status;              // int status word + barrier words
     pmd::DevBuf s_nbr, s_nnb, s_dedr, s_qf, s_vh, s_order, s_Ls, s_result;
     pmd::DevBuf s_noise;             // Gaussian increments of a parareal_correct window

@@ -8,7 +8,8 @@
 //    as a dataflow schedule with per-member dependencies (fine_flow), the FP64 path with bounded
 //    grid barriers between the phases (fine_loop).  Uneven interval lengths cost nothing beyond
 //    the active prefix.
-//  * COARSE (EAM): one CTA per member runs the whole interval in shared memory.
+//  * COARSE (Finnis-Sinclair EAM, or SNAP of band limit 2J = 2 for Strategy I): one CTA per
+//    member runs the whole interval in shared memory.
 //  * parareal_correct: one CTA walks the window sequentially (Algorithm 2's inner loop) with
 //    the same per-CTA coarse code, so C(cur_n) here equals C(prev_n) of the batched path bit
 //    for bit when the states are equal.
@@ -17,6 +18,7 @@
 #include "eam_device.cuh"
 #include "langevin_device.cuh"
 #include "pmd_internal.h"
+#include "snap_coarse.cuh"
 #include "snap_kernels.cuh"
 
 namespace pmd {
@@ -561,14 +563,14 @@ struct OwnState {
 constexpr int EAM_LIST_MAX_ATOMS = 512;   // systems up to this size keep a Verlet list in shared memory
 constexpr int EAM_PG_MAX_ATOMS = 256;     // ... and up to this size the FP32 pair-geometry cache
 
-__host__ __device__ inline size_t coarse_smem_bytes(int n) {
+__host__ __device__ inline size_t coarse_smem_bytes(int n, bool pg = true) {
     size_t b = (size_t)n * (3 * 8 + 16 + 3 * 8 + 8) + 64;
     if (n <= EAM_LIST_MAX_ATOMS) b += (size_t)n * (EAM_LIST_CAP * 2 + 1 + 16) + 64;
-    if (n <= EAM_PG_MAX_ATOMS) b += (size_t)n * (EAM_PG_CAP * (16 + 2) + 2) + 64;
-    return b;
+    if (pg && n <= EAM_PG_MAX_ATOMS) b += (size_t)n * (EAM_PG_CAP * (16 + 2) + 2) + 64;
+    return (b + 15) / 16 * 16;
 }
 
-__device__ inline EamShared coarse_carve(unsigned char* smem, int n) {
+__device__ inline EamShared coarse_carve(unsigned char* smem, int n, bool pg = true) {
     EamShared s;
     s.q = reinterpret_cast<double*>(smem);
     s.F = s.q + 3 * n;
@@ -586,13 +588,50 @@ __device__ inline EamShared coarse_carve(unsigned char* smem, int n) {
     s.pg = nullptr;
     s.pj = nullptr;
     s.pgc = nullptr;
-    if (n <= EAM_PG_MAX_ATOMS) {
+    if (pg && n <= EAM_PG_MAX_ATOMS) {
         s.pg = reinterpret_cast<float4*>(align_up(reinterpret_cast<size_t>(s.nbc + n), 16));
         s.pj = reinterpret_cast<unsigned short*>(s.pg + (size_t)n * EAM_PG_CAP);
         s.pgc = reinterpret_cast<unsigned char*>(s.pj + (size_t)n * EAM_PG_CAP);
     }
     return s;
 }
+
+// The coarse potential of the one-CTA kernels, passed by value to them: Finnis-Sinclair EAM, or
+// SNAP of a small band limit (Strategy I).  setup() runs once per launch with every thread
+// (tail: shared memory after the coarse state); refresh() keeps the Verlet list valid; forces()
+// fills s.F.  Both end with a CTA barrier.
+struct CoarseFS {
+    static constexpr bool PG = true;   // uses the FP32 pair-geometry cache of the EAM passes
+    FSDev fs;
+    __device__ __forceinline__ void setup(unsigned char*, int) {}
+    __device__ __forceinline__ void refresh(const EamShared& s, int n, const double box[3], bool force,
+                                            int* status) const {
+        eam_refresh_list(s, n, box, fs, force, status);
+    }
+    template <typename real, bool ONE>
+    __device__ __forceinline__ void forces(const EamShared& s, int n, const double box[3]) const {
+        eam_forces_cta<real, ONE>(s, n, box, fs, nullptr);
+    }
+};
+
+template <typename R, int TJ>
+struct CoarseSnap {
+    static constexpr bool PG = false;
+    SnapCoarseDev d;
+    SnapCoarseShared<R, TJ> t;
+    __device__ __forceinline__ void setup(unsigned char* tail, int n) {
+        t = snap_coarse_carve<R, TJ>(tail, n, d.nblk);
+        snap_coarse_load<R, TJ>(t, d);
+    }
+    __device__ __forceinline__ void refresh(const EamShared& s, int n, const double box[3], bool force,
+                                            int* status) const {
+        snap_coarse_refresh_list(s, n, box, d, force, status);
+    }
+    template <typename real, bool ONE>
+    __device__ __forceinline__ void forces(const EamShared& s, int n, const double box[3]) const {
+        snap_coarse_forces_cta<R, TJ>(s, t, n, box, d);
+    }
+};
 
 // G_{l,n} of atom i: from the precomputed window buffer [L+1][3][n] of this interval, or drawn
 template <int KMAX>
@@ -609,9 +648,9 @@ __device__ __forceinline__ void coarse_noise(const LangevinDev& L, const double*
 // Runs nsteps sub-steps of interval nid on the CTA-resident state (positions in s.q/s.qf,
 // velocities in own.v).  All threads call it.  list_ok tracks whether the CTA's Verlet list has
 // been built (it persists across intervals of a sweep).
-template <typename real, int KMAX>
+template <typename real, int KMAX, class CP>
 __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int n, const double box[3],
-                                    const FSDev& fs, const LangevinDev& L, int nsteps, int64_t nid, const double* Gpre,
+                                    const CP& pot, const LangevinDev& L, int nsteps, int64_t nid, const double* Gpre,
                                     bool& list_ok, int* status) {
     if (nsteps <= 0) return;
     // the Gaussian increments are loaded before the force evaluation that precedes their use
@@ -621,9 +660,9 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
         const int i = threadIdx.x + k * blockDim.x;
         if (i < n) coarse_noise<KMAX>(L, Gpre, nid, 0, i, n, Gc[k]);
     }
-    eam_refresh_list(s, n, box, fs, !list_ok, status);
+    pot.refresh(s, n, box, !list_ok, status);
     list_ok = true;
-    eam_forces_cta<real, KMAX == 1>(s, n, box, fs, nullptr);
+    pot.template forces<real, KMAX == 1>(s, n, box);
     bool bad = false;
     if (L.scheme == PMD_SCHEME_PAPER) {
 #pragma unroll
@@ -654,8 +693,8 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 if (i < n) coarse_noise<KMAX>(L, Gpre, nid, ell + 1, i, n, Gc[k]);
             }
             __syncthreads();
-            eam_refresh_list(s, n, box, fs, false, status);
-            eam_forces_cta<real, KMAX == 1>(s, n, box, fs, nullptr);
+            pot.refresh(s, n, box, false, status);
+            pot.template forces<real, KMAX == 1>(s, n, box);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
@@ -691,8 +730,8 @@ __device__ void coarse_interval_cta(const EamShared& s, OwnState<KMAX>& own, int
                 if (i < n && ell + 1 < nsteps) coarse_noise<KMAX>(L, Gpre, nid, ell + 1, i, n, Gc[k]);
             }
             __syncthreads();
-            eam_refresh_list(s, n, box, fs, false, status);
-            eam_forces_cta<real, KMAX == 1>(s, n, box, fs, nullptr);
+            pot.refresh(s, n, box, false, status);
+            pot.template forces<real, KMAX == 1>(s, n, box);
 #pragma unroll
             for (int k = 0; k < KMAX; ++k) {
                 const int i = threadIdx.x + k * blockDim.x;
@@ -734,12 +773,13 @@ __device__ void store_state(const EamShared& s, const OwnState<KMAX>& own, int n
     }
 }
 
-template <typename real, int KMAX>
-__global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_coarse_batch(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, double* q, double* v,
+template <typename real, int KMAX, class CP>
+__global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_coarse_batch(int n, double b0, double b1, double b2, CP pot, LangevinDev L, double* q, double* v,
                                long stride, const int32_t* __restrict__ nsteps, const int64_t* __restrict__ ids,
                                int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const EamShared s = coarse_carve(smem, n);
+    const EamShared s = coarse_carve(smem, n, CP::PG);
+    pot.setup(smem + coarse_smem_bytes(n, CP::PG), n);
     const double box[3] = {b0, b1, b2};
     const int m = blockIdx.x;
     int Lm = nsteps[m];
@@ -750,7 +790,7 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_coarse_batch(int n, d
     OwnState<KMAX> own;
     load_state<KMAX>(s, own, n, q + m * stride, v + m * stride, box);
     bool list_ok = false;
-    coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, Lm, ids[m], nullptr, list_ok, status);
+    coarse_interval_cta<real, KMAX>(s, own, n, box, pot, L, Lm, ids[m], nullptr, list_ok, status);
     store_state<KMAX>(s, own, n, q + m * stride, v + m * stride);
 }
 
@@ -761,25 +801,71 @@ static void coarse_shape(int n, int& threads, int& kmax) {
     kmax = (n + threads - 1) / threads;
 }
 
+// Device view of the engine's SNAP coarse context (Strategy I).
+static SnapCoarseDev make_snap_coarse(const pmd_engine* e) {
+    const pmd_snap* s = e->csnap;
+    SnapCoarseDev d{};
+    d.jobs = s->d_jobs.as<int4>();
+    d.round_tb = s->d_roundtb.as<unsigned char>();
+    d.cg = s->d_cg.p;
+    d.beffptr = s->d_beffptr.as<int>();
+    d.befft = s->d_befft.as<int>();
+    d.beffc = s->d_beffc.as<double>();
+    d.beta = e->cbeta.as<double>();
+    d.nrounds = s->T.nrounds;
+    d.ncg = (int)s->T.cg.size();
+    d.nblk = (int)s->T.blk_ta.size();
+    d.rcut = s->p.rcut;
+    d.kappa = s->p.rfac0 * PI / s->p.rcut;
+    d.switchflag = s->p.switchflag;
+    const double rm = s->p.rcut + 1e-3;
+    d.screen2 = (float)(rm * rm);
+    return d;
+}
+
+// Calls go(kernel, potential, shared bytes) with the coarse kernel instantiation of the engine's
+// coarse potential, precision and atoms per thread.
+template <template <typename, int, class> class K, class Go>
+static int coarse_dispatch(const pmd_engine* e, int n, int kmax, Go&& go) {
+    if (e->p.coarse_kind == PMD_COARSE_SNAP) {
+        if (kmax != 1 || n > EAM_LIST_MAX_ATOMS) return fail(PMD_EUNSUPPORTED, "the SNAP coarse potential supports at most 512 atoms");
+        const SnapCoarseDev d = make_snap_coarse(e);
+        if (e->p.coarse_snap.precision == PMD_FP64) {
+            CoarseSnap<double, 2> cp{d, {}};
+            return go(K<double, 1, CoarseSnap<double, 2>>::ptr(), cp,
+                      coarse_smem_bytes(n, false) + snap_coarse_smem_bytes<double, 2>(n, d.ncg, d.nblk));
+        }
+        CoarseSnap<float, 2> cp{d, {}};
+        return go(K<float, 1, CoarseSnap<float, 2>>::ptr(), cp,
+                  coarse_smem_bytes(n, false) + snap_coarse_smem_bytes<float, 2>(n, d.ncg, d.nblk));
+    }
+    const CoarseFS cp{make_fs(e->p.coarse)};
+    const bool f64 = e->p.coarse.precision == PMD_FP64;
+    const size_t sm = coarse_smem_bytes(n);
+    if (kmax == 1) return f64 ? go(K<double, 1, CoarseFS>::ptr(), cp, sm) : go(K<float, 1, CoarseFS>::ptr(), cp, sm);
+    if (kmax == 2) return f64 ? go(K<double, 2, CoarseFS>::ptr(), cp, sm) : go(K<float, 2, CoarseFS>::ptr(), cp, sm);
+    if (kmax <= 4) return f64 ? go(K<double, 4, CoarseFS>::ptr(), cp, sm) : go(K<float, 4, CoarseFS>::ptr(), cp, sm);
+    return fail(PMD_EUNSUPPORTED, "coarse propagation supports at most 2048 atoms");
+}
+
+template <typename real, int KMAX, class CP>
+struct CoarseBatchK {
+    static auto ptr() { return &k_coarse_batch<real, KMAX, CP>; }
+};
+
 int coarse_propagate(pmd_engine* e, int nbatch, int n, double* q, double* v, long stride, const int32_t* nsteps,
                      const int64_t* ids, const pmd_langevin& lp, cudaStream_t st) {
     int threads, kmax;
     coarse_shape(n, threads, kmax);
-    const size_t sm = coarse_smem_bytes(n);
-    const FSDev fs = make_fs(e->p.coarse);
     const LangevinDev L = make_langevin(lp);
-    const bool f64 = e->p.coarse.precision == PMD_FP64;
     const double* B = e->p.box;
-    auto go = [&](auto kern) -> int {
+    auto go = [&](auto kern, auto cp, size_t sm) -> int {
         PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        kern<<<nbatch, threads, sm, st>>>(n, B[0], B[1], B[2], fs, L, q, v, stride, nsteps, ids, e->status.as<int>());
+        kern<<<nbatch, threads, sm, st>>>(n, B[0], B[1], B[2], cp, L, q, v, stride, nsteps, ids, e->status.as<int>());
         PMD_CUDA_TRY(cudaGetLastError());
         return PMD_OK;
     };
-    if (kmax == 1) return f64 ? go(k_coarse_batch<double, 1>) : go(k_coarse_batch<float, 1>);
-    if (kmax == 2) return f64 ? go(k_coarse_batch<double, 2>) : go(k_coarse_batch<float, 2>);
-    if (kmax <= 4) return f64 ? go(k_coarse_batch<double, 4>) : go(k_coarse_batch<float, 4>);
-    return fail(PMD_EUNSUPPORTED, "coarse propagation supports at most 2048 atoms");
+    return coarse_dispatch<CoarseBatchK>(e, n, kmax, go);
 }
 
 // ---- parareal correction sweep ---------------------------------------------------------------
@@ -820,13 +906,14 @@ __device__ double cta_max(double x, double* red) {
     return red[32];
 }
 
-template <typename real, int KMAX>
-__global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_parareal_sweep(int n, double b0, double b1, double b2, FSDev fs, LangevinDev L, int nsteps, int n_in,
+template <typename real, int KMAX, class CP>
+__global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_parareal_sweep(int n, double b0, double b1, double b2, CP pot, LangevinDev L, int nsteps, int n_in,
                                  int n_fin, const double* __restrict__ jumps, const double* __restrict__ prev,
                                  double* __restrict__ cur, double* __restrict__ cout, double delta_expl, int metric,
                                  const double* __restrict__ Gwin, SweepResult* res, int* status) {
     extern __shared__ __align__(16) unsigned char smem[];
-    const EamShared s = coarse_carve(smem, n);
+    const EamShared s = coarse_carve(smem, n, CP::PG);
+    pot.setup(smem + coarse_smem_bytes(n, CP::PG), n);
     __shared__ double red[33];
     const double box[3] = {b0, b1, b2};
     const long S = 6L * n;
@@ -876,7 +963,7 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_parareal_sweep(int n,
 #pragma unroll
             for (int al = 0; al < 3; ++al) Po[k][al] = i < n ? P[al * n + i] : 0.0;
         }
-        coarse_interval_cta<real, KMAX>(s, own, n, box, fs, L, nsteps, (int64_t)nn, Gp, list_ok, status);
+        coarse_interval_cta<real, KMAX>(s, own, n, box, pot, L, nsteps, (int64_t)nn, Gp, list_ok, status);
         // jump, writes and error sums on the owning thread of each atom (the force evaluation
         // ended with a CTA barrier, so no thread still reads q)
         double a = 0.0, b = 0.0, mx = 0.0;
@@ -956,6 +1043,11 @@ __global__ void k_noise_window(uint64_t seed, int64_t n0, int count, int L1, int
     }
 }
 
+template <typename real, int KMAX, class CP>
+struct SweepK {
+    static auto ptr() { return &k_parareal_sweep<real, KMAX, CP>; }
+};
+
 int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, const double* prev, double* cur,
                    double* cout, double delta_expl, int metric, int L, const pmd_langevin& lp, double* delta_host,
                    int* n_stop_host, cudaStream_t st) {
@@ -964,10 +1056,7 @@ int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, cons
     coarse_shape(n, threads, kmax);
     threads = std::max(threads, 64);
     kmax = (n + threads - 1) / threads;
-    const size_t sm = coarse_smem_bytes(n);
-    const FSDev fs = make_fs(e->p.coarse);
     const LangevinDev Ld = make_langevin(lp);
-    const bool f64 = e->p.coarse.precision == PMD_FP64;
     const double* B = e->p.box;
     SweepResult* res = e->s_result.as<SweepResult>();
     // the window's Gaussian increments, drawn by the whole GPU ahead of the sequential sweep
@@ -983,18 +1072,14 @@ int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, cons
         k_noise_window<<<(unsigned)blocks, 256, 0, st>>>(lp.seed, (int64_t)n_in, count, L + 1, n, Gwin);
         PMD_CUDA_TRY(cudaGetLastError());
     }
-    auto go = [&](auto kern) -> int {
+    auto go = [&](auto kern, auto cp, size_t sm) -> int {
         PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        kern<<<1, threads, sm, st>>>(n, B[0], B[1], B[2], fs, Ld, L, n_in, n_fin, jumps, prev, cur, cout, delta_expl,
+        kern<<<1, threads, sm, st>>>(n, B[0], B[1], B[2], cp, Ld, L, n_in, n_fin, jumps, prev, cur, cout, delta_expl,
                                      metric, Gwin, res, e->status.as<int>());
         PMD_CUDA_TRY(cudaGetLastError());
         return PMD_OK;
     };
-    int rc;
-    if (kmax == 1) rc = f64 ? go(k_parareal_sweep<double, 1>) : go(k_parareal_sweep<float, 1>);
-    else if (kmax == 2) rc = f64 ? go(k_parareal_sweep<double, 2>) : go(k_parareal_sweep<float, 2>);
-    else if (kmax <= 4) rc = f64 ? go(k_parareal_sweep<double, 4>) : go(k_parareal_sweep<float, 4>);
-    else return fail(PMD_EUNSUPPORTED, "parareal_correct supports at most 2048 atoms");
+    int rc = coarse_dispatch<SweepK>(e, n, kmax, go);
     if (rc) return rc;
     SweepResult* h = static_cast<SweepResult*>(e->pinned);
     PMD_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(SweepResult), cudaMemcpyDeviceToHost, st));

@@ -1,5 +1,6 @@
-"""Write tests/golden/beta_fs_w_2j8.txt and beta_fs_w_2j6.txt: SNAP coefficients (2J = 8, 1 + 55
-values; 2J = 6, 1 + 30 values) fitted by ridge regression (lambda = 1e-6) to Finnis-Sinclair
+"""Write tests/golden/beta_fs_w_2j8.txt, beta_fs_w_2j6.txt and beta_fs_w_2j2.txt: SNAP coefficients
+(2J = 8, 1 + 55 values; 2J = 6, 1 + 30 values; 2J = 2, 1 + 5 values, the SNAP-6 coarse potential
+of Strategy I) fitted by ridge regression (lambda = 1e-6) to Finnis-Sinclair
 tungsten energies and forces, computed with the FP64 oracle only.
 
 Why: random coefficients beta_t ~ N(0, 0.01^2) give a SNAP without a repulsive core; the
@@ -11,7 +12,7 @@ members each at 300, 800, 1500, 2200 and 3000 K, Langevin EAM dynamics (paper sc
 schedule, dt 2 fs, gamma 5/ps) sampled after 100, 200 and 300 steps: 60 configurations.
 Rows: energy per atom (weight 1) and every force component (weight 1).
 
-2J = 6 (config 4's recipe, small): workloads.fit_starts(master=6, groups=4, members=4) -- four
+2J = 6 and 2J = 2 (config 4's recipe, small): workloads.fit_starts(master=6, groups=4, members=4) -- four
 temperatures drawn in 500-3000 K, each with four cells whose <111> dumbbell sits at a random
 site along a random <111> axis, 0.02 Angstrom displacements -- then the same Langevin EAM
 dynamics (dt 2 fs, gamma 5/ps, seed 1000 + group, interval ids 4 k + m) sampled after 100, 200
@@ -32,6 +33,7 @@ import workloads as W  # noqa: E402
 
 OUT = os.path.join(HERE, "beta_fs_w_2j8.txt")
 OUT6 = os.path.join(HERE, "beta_fs_w_2j6.txt")
+OUT2 = os.path.join(HERE, "beta_fs_w_2j2.txt")
 
 
 def training_set(master=4):
@@ -91,10 +93,13 @@ def write(path, beta, twojmax, nt):
 
 
 if __name__ == "__main__":
-    which = sys.argv[1:] or ["8", "6"]
+    which = sys.argv[1:] or ["8", "6", "2"]
     if "8" in which:
         confs, box = training_set()
         write(OUT, fit(confs, box), 8, 55)
     if "6" in which:
         confs, box = training_set_cfg4()
         write(OUT6, fit(confs, box, twojmax=6), 6, 30)
+    if "2" in which:   # SNAP-6: the coarse potential of Strategy I, same training set as 2J = 6
+        confs, box = training_set_cfg4()
+        write(OUT2, fit(confs, box, twojmax=2), 2, 5)

@@ -59,6 +59,13 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.pmd_engine_get_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
     assert lib.pmd_engine_autotune(None, 1, 1, None, None, 3, None, None, None, 1, None, None, None) == P.PMD_EINVAL
     assert lib.pmd_engine_selftest_waits(None, 100, None) == P.PMD_EINVAL
+    # a SNAP coarse potential must have 2J = 2 (SNAP-6, Strategy I): rejected before any device work
+    ep = P.EngineParams(P.snap_params(), P.fs_params(), (ctypes.c_double * 3)(20.0, 20.0, 20.0), 129,
+                        P.COARSE_SNAP, P.snap_params(twojmax=4))
+    assert lib.pmd_engine_create(ctypes.byref(ep), ctypes.byref(h)) == P.PMD_EUNSUPPORTED
+    ep.coarse_kind = 7
+    assert lib.pmd_engine_create(ctypes.byref(ep), ctypes.byref(h)) == P.PMD_EINVAL
+    assert lib.pmd_engine_set_coarse_beta(None, None, None) == P.PMD_EINVAL
     box3 = (ctypes.c_double * 3)(10.0, 10.0, 10.0)
     assert lib.sia_locate(1, 0, 4, box3, None, 3, None, None, None, None, None) == P.PMD_EINVAL
     assert lib.sia_locate(1, 4, 0, box3, None, 12, None, None, None, None, None) == P.PMD_EINVAL

@@ -102,3 +102,46 @@ def test_correct_reports_explosion_and_nonfinite():
     jumps[0, 0, 3] = float("nan")
     d, ns = eng.parareal_correct(0, 3, jumps, prev, cur, cache, 1e9, P.METRIC_REL, 1, lp)
     assert ns == 0 and d == float("inf")
+
+
+DIST_WORKER = r"""
+import os, sys
+sys.path.insert(0, {root!r})
+import numpy as np, torch, torch.distributed as dist
+import paper_2212_10508_gb300 as P
+import workloads as W
+from paper_2212_10508_gb300.distributed import EngineOps, adaptive_parareal_dist
+torch.cuda.set_device(0)
+dist.init_process_group("nccl", init_method="tcp://127.0.0.1:{port}", rank=0, world_size=1)
+pos, box = W.bcc_sia(3)
+q0 = torch.as_tensor(W.displaced(pos, 0.05, W.rng(21, 1)), device="cuda")
+v0 = torch.as_tensor(W.velocities(pos.shape[1], 2000.0, W.rng(21, 2)), device="cuda")
+beta = torch.as_tensor(W.fitted_beta(), device="cuda")
+lp = P.langevin(dt=2e-3, gamma=1.0, T=2000.0, seed=31, schedule=P.SCHED_ROBUST)
+e1 = P.Engine(pos.shape[1], box, beta=beta)
+c1, s1 = P.adaptive_parareal(e1, q0, v0, 12, 2, 1e-10, 2e-3, lp, metric=P.METRIC_MAXDISP)
+e2 = P.Engine(pos.shape[1], box, beta=beta)
+c2, s2 = adaptive_parareal_dist(EngineOps(e2, 2, lp, P.METRIC_MAXDISP), q0, v0, 12, 1e-10, 2e-3)
+e1.sync_status(); e2.sync_status()
+assert torch.equal(c1, c2), float((c1 - c2).abs().max())
+assert s1.log() == s2.log() and len({{e[3] for e in s1.log()}}) > 1, s1.log()
+dist.destroy_process_group()
+print("ok")
+"""
+
+
+def test_distributed_driver_with_engine_equals_single_gpu_driver():
+    """The multi-rank driver (EngineOps, NCCL process group of one rank) gives, bit for bit, the
+    single-GPU adaptive_parareal's states and slab log (several slabs)."""
+    import os
+    import socket
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    env = dict(os.environ, MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), NCCL_NVLS_ENABLE="0")
+    r = subprocess.run([sys.executable, "-c", DIST_WORKER.format(root=root, port=port)], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]

@@ -133,8 +133,9 @@ GOLDEN = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))
 
 def fitted_beta(twojmax: int = 8):
     """SNAP coefficients (1 + nB) fitted to Finnis-Sinclair W by the oracle: 2J = 8 (the bench's
-    potential) or 2J = 6 (config 4's recipe); see tests/golden/make_fitted_beta.py."""
-    name = {8: "beta_fs_w_2j8.txt", 6: "beta_fs_w_2j6.txt"}[twojmax]
+    potential), 2J = 6 (config 4's recipe) or 2J = 2 (SNAP-6, the coarse potential of Strategy I);
+    see tests/golden/make_fitted_beta.py."""
+    name = {8: "beta_fs_w_2j8.txt", 6: "beta_fs_w_2j6.txt", 2: "beta_fs_w_2j2.txt"}[twojmax]
     vals = [float(ln) for ln in open(os.path.join(GOLDEN, name)) if ln.strip() and ln[0] != "#"]
     return np.array(vals)
 
