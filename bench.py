@@ -49,7 +49,7 @@ CPU_SAMPLES = {"cfg2": (8, 100), "cfg3": (2, 20)}
 CPU_SAMPLES_1T = {"cfg2": (1, 100), "cfg3": (1, 10)}
 
 
-KERNEL_SOURCES = ("propagate.cu", "snap.cu", "snap_kernels.cuh", "snap_batch.cuh", "snap_v2.cuh", "snap_device.cuh",
+KERNEL_SOURCES = ("propagate.cu", "snap.cu", "snap_launch.cuh", "snap_kernels.cuh", "snap_batch.cuh", "snap_v2.cuh", "snap_device.cuh",
                   "device_common.cuh", "langevin_device.cuh", "eam_device.cuh", "pmd_internal.h", "status_bits.h")
 
 
@@ -281,12 +281,28 @@ def _parareal(P, W, dev, torch, Nh=300, ncell=5, T=1500.0):
     t_f = t_seq / Nh
     cost, g_ad, g_id = st.cost(t_f, t_c)
     log = st.log()
+    # the fine batches alone: one launch of each slab width the run used, timed, times the number
+    # of iterations on that width (the bound a free correction sweep would leave)
+    width_ms = {}
+    batch = cur[:Nh].clone()
+    for (a, b, k, _) in log:
+        w = b - a
+        if w not in width_ms:
+            ns = torch.full((w,), L, dtype=torch.int32, device=dev)
+            eng.baoab_propagate_batch(P.FINE, batch[:w], None, ns, ids[:w], lp)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            eng.baoab_propagate_batch(P.FINE, batch[:w], None, ns, ids[:w], lp)
+            torch.cuda.synchronize()
+            width_ms[w] = (time.perf_counter() - t0) * 1e3
+    t_fine_batches = sum(k * width_ms[b - a] for (a, b, k, _) in log) / 1e3
     return {"workload": "251-atom W+SIA (5^3 cells), SNAP 2J=8 fitted (FP32-bulk) fine, FS EAM (FP32-bulk) coarse, "
                         "dt 1 fs, L=1, 1500 K, gamma 1/ps, schedule C0=C1=2, N=%d intervals" % Nh,
             "delta_conv_A": dconv, "delta_expl_A": dexpl, "metric": "max per-atom displacement (A)",
             "wall_sequential_s": t_seq, "wall_parareal_s": t_par, "speedup": t_seq / t_par,
             "n_slab": (log[-1][3] + 1) if log else 0, "iterations": int(sum(e[2] for e in log)),
             "C_f_ms": t_f * 1e3, "C_c_ms": t_c * 1e3, "gamma_adapt_eq8": g_ad, "gamma_ideal_eq9": g_id,
+            "fine_batches_s": t_fine_batches, "speedup_bound_free_sweeps": t_seq / t_fine_batches,
             "final_max_dq_vs_sequential_A": float((cur[Nh, :3] - ref[0, :3]).abs().max().item())}
 
 

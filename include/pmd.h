@@ -47,7 +47,8 @@ enum {
 };
 
 #define PMD_MAX_NEIGHBORS 64      /* per-atom neighbour capacity of the SNAP and EAM kernels */
-#define PMD_MAX_TWOJMAX 8         /* largest 2J the SNAP kernels are built for */
+#define PMD_MAX_TWOJMAX 14        /* largest 2J the SNAP kernels are built for (2J > 8: FP64 and
+                                     snap_energy_forces only; 14 is the paper's SNAP-205) */
 #define PMD_MAX_COARSE_ATOMS 2048 /* largest system the one-CTA coarse propagator accepts */
 
 enum { PMD_FP64 = 0, PMD_FP32_BULK = 1 };            /* arithmetic of the potential kernels */
@@ -66,7 +67,8 @@ enum { PMD_METRIC_REL = 0, PMD_METRIC_MAXDISP = 1 };
  * bispectrum B_{j1 j2 j} (0 <= j2 <= j1 <= j <= twojmax/2) of the weighted density
  * I + sum_k fc(r_k) U(a_k, b_k), fc = (cos(pi r/rcut)+1)/2, enters E_i = beta_0 + sum_t beta_t B_t. */
 typedef struct {
-    int twojmax;      /* 2J, 0..PMD_MAX_TWOJMAX (8 gives the 55 components of SNAP-56) */
+    int twojmax;      /* 2J, even, 2..PMD_MAX_TWOJMAX (8 gives the 55 components of SNAP-56, 14 the
+                         204 of SNAP-205); above 8 FP64 only, and no engine (propagation) */
     double rcut;      /* Angstrom */
     double rfac0;     /* in (0, 1] */
     double rmin0;     /* must be 0 */
@@ -229,11 +231,14 @@ int pmd_engine_selftest_waits(pmd_engine* e, long long polls, pmd_stream_t strea
  *                rows per warp (half-warps of 16 atoms), rows4_atoms (0..8) with four rows per warp;
  *   b_group      atoms per warp in the integrator phase (1..10);
  *   noise_stage  Y stage (by sub-block size tb, 0 = tb <= 3) that also draws the Gaussian
- *                increments of the batch, -1 = the stage of tb = 6.
+ *                increments of the batch, -1 = the stage of tb = 6;
+ *   warps        warps per CTA of the persistent kernel, 16 (up to 128 registers per thread) or
+ *                8 (up to 255: no register spills, half the warps to hide latency); 8 is built
+ *                for 2J = 8 only, other band limits run with 16.
  * Results do not depend on the shape (every output keeps its arithmetic and order); only time
- * does.  Defaults {16, 8, 8, -1}. */
+ * does.  Defaults {16, 8, 8, -1, 16}. */
 typedef struct {
-    int rows2_atoms, rows4_atoms, b_group, noise_stage;
+    int rows2_atoms, rows4_atoms, b_group, noise_stage, warps;
 } pmd_fine_tuning;
 int pmd_engine_get_tuning(const pmd_engine* e, pmd_fine_tuning* out);
 int pmd_engine_set_tuning(pmd_engine* e, const pmd_fine_tuning* t);

@@ -67,7 +67,7 @@ class EngineParams(ctypes.Structure):
 class FineTuning(ctypes.Structure):
     """Run-time shape of the batched FP32 fine kernel (pmd_fine_tuning)."""
     _fields_ = [("rows2_atoms", ctypes.c_int), ("rows4_atoms", ctypes.c_int), ("b_group", ctypes.c_int),
-                ("noise_stage", ctypes.c_int)]
+                ("noise_stage", ctypes.c_int), ("warps", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -70,8 +70,10 @@ int jumps_launch(long count, const double* f, const double* c, double* j, int nu
 
 static int check_snap_params(const pmd_snap_params* p) {
     if (!p) return fail(PMD_EINVAL, "SNAP parameters are NULL");
-    if (p->twojmax != 2 && p->twojmax != 4 && p->twojmax != 6 && p->twojmax != 8)
-        return fail(PMD_EUNSUPPORTED, "twojmax must be 2, 4, 6 or 8");
+    if (p->twojmax < 2 || p->twojmax > PMD_MAX_TWOJMAX || (p->twojmax & 1))
+        return fail(PMD_EUNSUPPORTED, "twojmax must be 2, 4, ..., 14");
+    if (p->twojmax > 8 && p->precision != PMD_FP64)
+        return fail(PMD_EUNSUPPORTED, "twojmax > 8 is available in FP64 only");
     if (!(p->rcut > 0) || !(p->rfac0 > 0 && p->rfac0 <= 1) || p->rmin0 != 0.0)
         return fail(PMD_EINVAL, "need rcut > 0, 0 < rfac0 <= 1 and rmin0 == 0");
     if (p->switchflag != 0 && p->switchflag != 1) return fail(PMD_EINVAL, "switchflag must be 0 or 1");
@@ -226,6 +228,9 @@ int pmd_engine_create(const pmd_engine_params* p, pmd_engine** out) {
     if (p->coarse_kind != PMD_COARSE_FS && !csnap) return fail(PMD_EINVAL, "pmd_engine_create: bad coarse_kind");
     if ((rc = check_snap_params(&p->fine)) || (rc = csnap ? check_snap_params(&p->coarse_snap) : check_fs(&p->coarse)))
         return rc;
+    if (p->fine.twojmax > 8)
+        return fail(PMD_EUNSUPPORTED, "pmd_engine_create: the fine propagator supports twojmax <= 8 "
+                                      "(larger band limits: snap_energy_forces)");
     if (p->natoms < 1 || p->natoms > PMD_MAX_COARSE_ATOMS)
         return fail(PMD_EUNSUPPORTED, "pmd_engine_create: natoms must be in 1..PMD_MAX_COARSE_ATOMS");
     if (csnap && (p->coarse_snap.twojmax != 2 || p->natoms > 512))

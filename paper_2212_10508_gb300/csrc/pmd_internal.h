@@ -130,7 +130,7 @@ struct pmd_engine {
     int num_sms = 0;
     void* pinned = nullptr;          // small pinned host buffer for parareal_correct results
     int profile = 0;                 // record events around the persistent FINE kernel
-    pmd_fine_tuning tune = {16, 8, 8, -1};   // run-time shape of the batched FP32 kernel (autotuned)
+    pmd_fine_tuning tune = {16, 8, 8, -1, 16};   // run-time shape of the batched FP32 kernel (autotuned)
     int prof_recorded = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };

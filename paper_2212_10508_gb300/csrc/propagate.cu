@@ -446,8 +446,8 @@ __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
     }
 }
 
-template <typename real, int TJ>
-__global__ void __launch_bounds__(snap_cta_threads<real>(), 1) k_fine_persistent(FineArgs a) {
+template <typename real, int TJ, int NTH = snap_cta_threads<real, TJ>()>
+__global__ void __launch_bounds__(NTH, 1) k_fine_persistent(FineArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     if constexpr (sizeof(real) == 4) {
         SBShared<TJ> sh = sb_shared_carve<TJ>(smem, a.v);
@@ -509,9 +509,13 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
                                                                      a.qf);
         PMD_CUDA_TRY(cudaGetLastError());
     }
-    constexpr int threads = snap_cta_threads<real>();
+    // FP32, 2J = 8: the CTA size is a tuning knob (16 warps, or 8 with twice the registers)
+    const bool half = sizeof(real) == 4 && TJ == 8 && e->tune.warps == 8;
+    const int threads = half ? SB_THREADS / 2 : snap_cta_threads<real, TJ>();
     const size_t sm = sizeof(real) == 4 ? sb_shared_bytes<TJ>(a.v) : snap_shared_bytes<real, TJ>(a.v, threads / 32);
-    auto kern = k_fine_persistent<real, TJ>;
+    void (*kern)(FineArgs) = k_fine_persistent<real, TJ>;
+    if constexpr (sizeof(real) == 4 && TJ == 8)
+        if (half) kern = k_fine_persistent<real, TJ, SB_THREADS / 2>;
     PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     int per_sm = 0;
     PMD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, sm));

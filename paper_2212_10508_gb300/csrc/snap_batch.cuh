@@ -24,7 +24,7 @@ namespace pmd {
 
 constexpr int SB_ATOMS = 32;              // atoms per batch = lanes of the Y phase
 constexpr int SB_LD = 33;                 // leading dimension of the [element][atom] arrays
-constexpr int SB_WARPS = 16;
+constexpr int SB_WARPS = 16;             // warps per CTA (at most; the fine kernel also runs with 8)
 constexpr int SB_THREADS = SB_WARPS * 32;
 constexpr int SB_CHUNK = 8;               // U-pass elements summed per lane-sum round (4 lanes each)
 constexpr int SB_SMALL_TB = 3;            // sub-block sizes tb <= this share one Y stage
@@ -544,8 +544,9 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const SBTables& tb, const SnapD
     const float kappa = float(sp.rfac0 * PI / sp.rcut);
     const float rcut = float(sp.rcut);
 
+    const int nwarps = blockDim.x >> 5;   // SB_WARPS or fewer (the CTA size is a tuning knob)
     // U phase
-    for (int slot = warp; slot < SB_ATOMS; slot += SB_WARPS) {
+    for (int slot = warp; slot < SB_ATOMS; slot += nwarps) {
         if (slot >= na) {   // empty slot: a zero column keeps the Y phase finite
             for (int f = lane; f < NF; f += 32) sh.ut[f * SB_LD + slot] = make_float2(0.f, 0.f);
             continue;
@@ -589,7 +590,7 @@ __device__ void sb_batch(const SBShared<TJ>& sh, const SBTables& tb, const SnapD
     sb_fill_middle<TJ>(sh.yt);
 
     // dE/dr phase
-    for (int slot = warp; slot < na; slot += SB_WARPS) {
+    for (int slot = warp; slot < na; slot += nwarps) {
         const SBAtom A = at(slot);
         float2* yw = sh.yw(warp);
         sb_weight_y<TJ>(sh.yt, slot, yw, sh.tab, lane);

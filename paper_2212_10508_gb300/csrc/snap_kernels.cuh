@@ -37,17 +37,29 @@ struct SnapShared {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// The Clebsch-Gordan values sit in shared memory up to 2J = 8; from 2J = 10 on (80 KB and more)
+// the kernels read them from global memory through the caches.
+template <int TJ>
+__host__ __device__ constexpr bool snap_cg_shared() { return TJ <= 8; }
+
 template <typename real, int TJ>
 __host__ __device__ inline size_t snap_table_bytes(const SnapView& v) {
     size_t o = 0;
-    o = align_up(o + (size_t)v.ncg * sizeof(real), 32);
+    if (snap_cg_shared<TJ>()) o = align_up(o + (size_t)v.ncg * sizeof(real), 32);
     o = align_up(o + (size_t)v.nblk * sizeof(real), 32);
     o = align_up(o + (size_t)Dims<TJ>::NHALF * sizeof(ElemRT<real>), 32);
     return o;
 }
 
+// threads per CTA of the SNAP kernels: the batched FP32 design, or one warp per atom (FP64; two
+// warps per CTA from 2J = 10 on, whose per-warp scratch is 27-62 KB)
+template <typename real, int TJ = 8>
+__host__ __device__ constexpr int snap_cta_threads() {
+    return sizeof(real) == 4 ? SB_THREADS : (TJ <= 8 ? SNAP_THREADS : 64);
+}
+
 template <typename real, int TJ>
-__host__ __device__ inline size_t snap_shared_bytes(const SnapView& v, int nwarps = SNAP_THREADS / 32) {
+__host__ __device__ inline size_t snap_shared_bytes(const SnapView& v, int nwarps = snap_cta_threads<real, TJ>() / 32) {
     return snap_table_bytes<real, TJ>(v) + (size_t)nwarps * sizeof(WarpScratch2<real, TJ>);
 }
 
@@ -55,8 +67,12 @@ template <typename real, int TJ>
 __device__ inline SnapShared<real, TJ> snap_shared_carve(unsigned char* smem, const SnapView& v) {
     SnapShared<real, TJ> sh;
     size_t o = 0;
-    sh.cg = reinterpret_cast<real*>(smem + o);
-    o = align_up(o + (size_t)v.ncg * sizeof(real), 32);
+    if (snap_cg_shared<TJ>()) {
+        sh.cg = reinterpret_cast<real*>(smem + o);
+        o = align_up(o + (size_t)v.ncg * sizeof(real), 32);
+    } else {
+        sh.cg = const_cast<real*>(reinterpret_cast<const real*>(v.cg));
+    }
     sh.beff = reinterpret_cast<real*>(smem + o);
     o = align_up(o + (size_t)v.nblk * sizeof(real), 32);
     sh.tab = reinterpret_cast<ElemRT<real>*>(smem + o);
@@ -70,7 +86,8 @@ __device__ inline SnapShared<real, TJ> snap_shared_carve(unsigned char* smem, co
 template <typename real, int TJ>
 __device__ inline void snap_shared_load(SnapShared<real, TJ>& sh, const SnapView& v) {
     const real* cg = reinterpret_cast<const real*>(v.cg);
-    for (int x = threadIdx.x; x < v.ncg; x += blockDim.x) sh.cg[x] = cg[x];
+    if (snap_cg_shared<TJ>())
+        for (int x = threadIdx.x; x < v.ncg; x += blockDim.x) sh.cg[x] = cg[x];
     for (int b = threadIdx.x; b < v.nblk; b += blockDim.x) {
         double s = 0.0;
         for (int c = v.beffptr[b]; c < v.beffptr[b + 1]; ++c) s += v.beffc[c] * v.beta[1 + v.befft[c]];
@@ -132,12 +149,6 @@ __device__ inline void sb_shared_load(SBShared<TJ>& sh, const SnapView& v) {
 
 inline __host__ __device__ SBTables sb_tables(const SnapView& v) {
     return SBTables{v.sbjobs, v.sbrows, v.sbsptr, v.sbcoef, v.sbgroups, v.sbgptr};
-}
-
-// threads per CTA of the SNAP kernels: the batched FP32 design or one warp per atom (FP64)
-template <typename real>
-__host__ __device__ constexpr int snap_cta_threads() {
-    return sizeof(real) == 4 ? SB_THREADS : SNAP_THREADS;
 }
 
 }  // namespace pmd

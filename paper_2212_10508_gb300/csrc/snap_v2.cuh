@@ -105,18 +105,19 @@ __host__ __device__ constexpr HM hm(int E) {
     return m;
 }
 
-template <int E, int N>
+// f.apply<E>() for E = B, ..., N - 1 in increasing order (split in halves: nesting depth log2 N, so
+// that the 652 elements of 2J = 14 stay within the compiler's instantiation depth).
+template <int B, int N>
 struct ForE {
     template <class F>
     __device__ __forceinline__ static void run(F& f) {
-        f.template apply<E>();
-        ForE<E + 1, N>::run(f);
+        if constexpr (N - B == 1) {
+            f.template apply<B>();
+        } else if constexpr (N - B > 1) {
+            ForE<B, B + (N - B) / 2>::run(f);
+            ForE<B + (N - B) / 2, N>::run(f);
+        }
     }
-};
-template <int N>
-struct ForE<N, N> {
-    template <class F>
-    __device__ __forceinline__ static void run(F&) {}
 };
 
 // ---- per-lane recursion -------------------------------------------------------------------------
@@ -322,22 +323,22 @@ __device__ __forceinline__ void y_job(const int4 J, const cplx<real>* __restrict
     yh[e].im += be * zi;
 }
 
-template <typename real>
+template <typename real, int TJ>
 __device__ __noinline__ void y_rounds(const int4* __restrict__ jobs, const unsigned char* __restrict__ round_tb,
                                          int nrounds, int lane, const cplx<real>* U, const real* cg, const real* beff,
                                          cplx<real>* yh) {
     for (int r = 0; r < nrounds; ++r) {
         const int4 J = jobs[r * 32 + lane];
         switch (round_tb[r]) {
-            case 0: y_job<real, 0>(J, U, cg, beff, yh); break;
-            case 1: y_job<real, 1>(J, U, cg, beff, yh); break;
-            case 2: y_job<real, 2>(J, U, cg, beff, yh); break;
-            case 3: y_job<real, 3>(J, U, cg, beff, yh); break;
-            case 4: y_job<real, 4>(J, U, cg, beff, yh); break;
-            case 5: y_job<real, 5>(J, U, cg, beff, yh); break;
-            case 6: y_job<real, 6>(J, U, cg, beff, yh); break;
-            case 7: y_job<real, 7>(J, U, cg, beff, yh); break;
-            default: y_job<real, 8>(J, U, cg, beff, yh); break;
+#define PMD_YR_CASE(TB_) \
+    case TB_:            \
+        if constexpr (TB_ <= TJ) y_job<real, TB_>(J, U, cg, beff, yh); \
+        break;
+            PMD_YR_CASE(0) PMD_YR_CASE(1) PMD_YR_CASE(2) PMD_YR_CASE(3) PMD_YR_CASE(4) PMD_YR_CASE(5)
+            PMD_YR_CASE(6) PMD_YR_CASE(7) PMD_YR_CASE(8) PMD_YR_CASE(9) PMD_YR_CASE(10) PMD_YR_CASE(11)
+            PMD_YR_CASE(12) PMD_YR_CASE(13) PMD_YR_CASE(14)
+#undef PMD_YR_CASE
+            default: break;
         }
     }
 }
@@ -487,7 +488,7 @@ __device__ __noinline__ void snap_atom_warp2(WarpScratch2<real, TJ>& ws, const E
     // Y = sum_blocks beta_eff Z (lockstep rounds, lane-owned outputs)
     for (int e = lane; e <= NH; e += 32) ws.yh[e] = {real(0), real(0)};
     __syncwarp();
-    y_rounds<real>(yt.jobs, yt.round_tb, yt.nrounds, lane, ws.full, cg, beff, ws.yh);
+    y_rounds<real, TJ>(yt.jobs, yt.round_tb, yt.nrounds, lane, ws.full, cg, beff, ws.yh);
     __syncwarp();
     expand_y<real, TJ>(ws.yh, ws.full, tab, lane);
     __syncwarp();

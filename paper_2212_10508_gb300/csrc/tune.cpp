@@ -1,7 +1,9 @@
 // Run-time shape of the batched FP32 fine kernel and its autotuner: a coordinate search over
 // the shape knobs (multi-row warp thresholds of the Y contraction, atoms per warp in the
-// integrator phase, the Y stage that draws the Gaussian increments), each candidate timed with
-// CUDA events on a length-scaled copy of the caller's batch.
+// integrator phase, the Y stage that draws the Gaussian increments, and the CTA size, which
+// selects one of two compiled instantiations of the kernel: 16 warps with at most 128 registers
+// per thread or 8 warps with up to 255), each candidate timed with CUDA events on a length-scaled
+// copy of the caller's batch.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -19,8 +21,9 @@ using namespace pmd;
 static int check_tuning(const pmd_fine_tuning* t) {
     if (!t) return fail(PMD_EINVAL, "tuning: NULL");
     if (t->rows2_atoms < 0 || t->rows2_atoms > 16 || t->rows4_atoms < 0 || t->rows4_atoms > 8 || t->b_group < 1 ||
-        t->b_group > 10 || t->noise_stage < -1 || t->noise_stage > 15)
-        return fail(PMD_EINVAL, "tuning: rows2_atoms 0..16, rows4_atoms 0..8, b_group 1..10, noise_stage -1..15");
+        t->b_group > 10 || t->noise_stage < -1 || t->noise_stage > 15 || (t->warps != 8 && t->warps != 16))
+        return fail(PMD_EINVAL, "tuning: rows2_atoms 0..16, rows4_atoms 0..8, b_group 1..10, noise_stage -1..15, "
+                                "warps 8 or 16");
     return PMD_OK;
 }
 
@@ -114,11 +117,13 @@ extern "C" int pmd_engine_autotune(pmd_engine* e, int nbatch, int natoms, const 
     double best_t = 0.0;
     rc = time_shape(best, &best_t);
     // coordinate search: each knob in turn over its candidates, keeping the fastest so far
-    const std::vector<std::vector<int>> cand = {{16, 12, 8, 0}, {8, 4, 0}, {8, 10, 6, 4}, {-1, 2, 4, 5, 1}};
-    for (int knob = 0; knob < 4 && !rc; ++knob)
+    std::vector<std::vector<int>> cand = {{16, 12, 8, 0}, {8, 4, 0}, {8, 10, 6, 4}, {-1, 2, 4, 5, 1}, {16, 8}};
+    if (e->p.fine.twojmax != 8) cand[4] = {16};   // the 8-warp kernel is built for 2J = 8
+    for (int knob = 0; knob < 5 && !rc; ++knob)
         for (int val : cand[knob]) {
             pmd_fine_tuning sh = best;
-            int* f = knob == 0 ? &sh.rows2_atoms : knob == 1 ? &sh.rows4_atoms : knob == 2 ? &sh.b_group : &sh.noise_stage;
+            int* f = knob == 0 ? &sh.rows2_atoms : knob == 1 ? &sh.rows4_atoms : knob == 2 ? &sh.b_group
+                                 : knob == 3 ? &sh.noise_stage : &sh.warps;
             if (*f == val) continue;
             *f = val;
             double t = 0.0;

@@ -43,6 +43,13 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     h = ctypes.c_void_p()
     bad = P.snap_params(twojmax=3)
     assert lib.pmd_snap_create(ctypes.byref(bad), ctypes.byref(h)) == P.PMD_EUNSUPPORTED
+    big32 = P.snap_params(twojmax=14, precision=P.FP32_BULK)      # 2J > 8: FP64 only
+    assert lib.pmd_snap_create(ctypes.byref(big32), ctypes.byref(h)) == P.PMD_EUNSUPPORTED
+    big = P.snap_params(twojmax=16)
+    assert lib.pmd_snap_create(ctypes.byref(big), ctypes.byref(h)) == P.PMD_EUNSUPPORTED
+    ep14 = P.EngineParams(P.snap_params(twojmax=14), P.fs_params(), (ctypes.c_double * 3)(20.0, 20.0, 20.0), 129,
+                          P.COARSE_FS, P.snap_params(twojmax=2))
+    assert lib.pmd_engine_create(ctypes.byref(ep14), ctypes.byref(h)) == P.PMD_EUNSUPPORTED
     bad = P.snap_params()
     bad.rmin0 = 0.5
     assert lib.pmd_snap_create(ctypes.byref(bad), ctypes.byref(h)) == P.PMD_EINVAL
@@ -54,7 +61,7 @@ def test_bad_arguments_are_rejected_on_the_host(lib):
     assert lib.eam_energy_forces(ctypes.byref(fs), 1, 10, small, None, None, None, None) == P.PMD_EINVAL
     assert lib.pmd_adaptive_create(10, 0.5, 0.1, ctypes.byref(h)) == P.PMD_EINVAL
     assert lib.adaptive_restart(None, 0.0, 0, None) == P.PMD_EINVAL
-    t = P.FineTuning(16, 8, 8, -1)
+    t = P.FineTuning(16, 8, 8, -1, 16)
     assert lib.pmd_engine_set_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
     assert lib.pmd_engine_get_tuning(None, ctypes.byref(t)) == P.PMD_EINVAL
     assert lib.pmd_engine_autotune(None, 1, 1, None, None, 3, None, None, None, 1, None, None, None) == P.PMD_EINVAL

@@ -25,10 +25,10 @@ def test_results_do_not_depend_on_shape(nb):
     # 3 members: few atoms per CTA (4-row warps), 20: 2-row warps, 64: full batches and the tail
     P, eng, q, v, L, ids, lp = _batch(nb, 5, 30)
     ref = None
-    shapes = [dict(rows2_atoms=16, rows4_atoms=8, b_group=8, noise_stage=-1),
-              dict(rows2_atoms=0, rows4_atoms=0, b_group=4, noise_stage=2),
-              dict(rows2_atoms=16, rows4_atoms=0, b_group=10, noise_stage=5),
-              dict(rows2_atoms=8, rows4_atoms=4, b_group=1, noise_stage=0)]
+    shapes = [dict(rows2_atoms=16, rows4_atoms=8, b_group=8, noise_stage=-1, warps=16),
+              dict(rows2_atoms=0, rows4_atoms=0, b_group=4, noise_stage=2, warps=16),
+              dict(rows2_atoms=16, rows4_atoms=0, b_group=10, noise_stage=5, warps=8),
+              dict(rows2_atoms=8, rows4_atoms=4, b_group=1, noise_stage=0, warps=8)]
     for sh in shapes:
         eng.set_tuning(**sh)
         qq, vv = q.clone(), v.clone()
@@ -47,12 +47,13 @@ def test_autotune_returns_valid_shape_and_keeps_inputs():
     assert torch.equal(q, q0) and torch.equal(v, v0) and torch.equal(L, L0)
     assert ms > 0
     assert 0 <= shape["rows2_atoms"] <= 16 and 0 <= shape["rows4_atoms"] <= 8
-    assert 1 <= shape["b_group"] <= 10 and -1 <= shape["noise_stage"] <= 15
+    assert 1 <= shape["b_group"] <= 10 and -1 <= shape["noise_stage"] <= 15 and shape["warps"] in (8, 16)
     assert eng.tuning() == shape
 
 
 def test_bad_shapes_rejected():
     P, eng, *_ = _batch(2, 5, 6)
-    for bad in (dict(rows2_atoms=17), dict(rows4_atoms=9), dict(b_group=0), dict(b_group=11), dict(noise_stage=-2)):
+    for bad in (dict(rows2_atoms=17), dict(rows4_atoms=9), dict(b_group=0), dict(b_group=11), dict(noise_stage=-2),
+                dict(warps=12)):
         with pytest.raises(P.PmdError):
             eng.set_tuning(**bad)

@@ -47,6 +47,16 @@ def test_snap_other_band_limits(twojmax, precision, tol):
     _compare_snap(P_, box, beta, twojmax, precision, tol)
 
 
+@pytest.mark.parametrize("twojmax", [10, 12, 14])
+def test_snap_large_band_limits_fp64(twojmax):
+    """2J = 10, 12 and 14 (14: the paper's SNAP-205 size, 204 bispectrum components), FP64 warp
+    per atom with the Clebsch-Gordan values in global memory: energies, forces and dE/dbeta of
+    two 129-atom configurations against the oracle at 1e-10."""
+    P_, box, _ = W.small_system(nconf=2)
+    beta = W.snap_beta(W.n_bispectrum(twojmax), W.rng(6, twojmax))
+    _compare_snap(P_, box, beta, twojmax, P.FP64, 1e-10)
+
+
 def test_snap_2001_atoms():
     pos, box = W.bcc_sia(10)
     pos = W.displaced(pos, 0.05, W.rng(7, 1), count=1)
