@@ -79,6 +79,7 @@ struct FineArgs {
     unsigned char* pos;     // reverse-slot tables [member][n][n], or nullptr (binary search)
     SBShape shape;          // FP32 path: run-time shape of the batched pass
     int b_group;            // atoms per warp in phase B (1..SB_B_GROUP_MAX)
+    int merge_b;            // FP32 path: large sub-steps run phase B on the CTA completing a member
     unsigned long long* flow;   // FP32 path (64-bit words, no wrap for any launch): [0] next item, [1] abort,
                                 //   [2, 2 + nbatch) atoms done in phase A
                             // per member (order position), [2 + nbatch, 2 + 2 nbatch) in phase B
@@ -326,16 +327,22 @@ struct FlowCursor {
     long base = 0;         // first item of the sub-step
     long nA = 0, nB = 0;   // its phase-A and phase-B items
     long bA = 1, bB = 1;   // and their sizes in atoms
+    int merged = 0;        // phase B run by the CTA that completes a member's phase A (no B items)
 };
 
+// A sub-step with at least one full wave of full batches runs each member's phase B on the CTA
+// whose batch completes the member's phase A (no phase-B items: no CTA takes a B item and waits
+// for a batch still running elsewhere); smaller sub-steps keep B items spread over the CTAs, which
+// keeps the chain A -> B -> A of few members short.
 __device__ __forceinline__ void flow_set(const FineArgs& a, FlowCursor& c, int bmax) {
     c.A = c.ell <= *a.Lmax ? active_members(a.Ls, a.nbatch, c.ell) : 0;
     const long items = (long)c.A * a.n;
     const long per = (items + gridDim.x - 1) / gridDim.x;
     c.bA = per < SB_ATOMS ? (per > 0 ? per : 1) : SB_ATOMS;
     c.bB = per < bmax ? (per > 0 ? per : 1) : bmax;
+    c.merged = a.merge_b && items >= (long)gridDim.x * SB_ATOMS;
     c.nA = (items + c.bA - 1) / c.bA;
-    c.nB = (items + c.bB - 1) / c.bB;
+    c.nB = c.merged ? 0 : (items + c.bB - 1) / c.bB;
 }
 
 // Thread 0: wait until *ctr >= target (bounded; one item takes < 1 ms, the limit ~4 s; the abort
@@ -372,7 +379,8 @@ int selftest_waits(pmd_engine* e, long long polls, cudaStream_t st) {
 
 template <int TJ>
 __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
-    __shared__ long s_item[4];   // sub-step, phase (0 A, 1 B, -1 done), items [first, end)
+    __shared__ long s_item[5];   // sub-step, phase (0 A, 1 B, -1 done), items [first, end), merged B
+    __shared__ int s_comp[SB_ATOMS + 2];   // merged mode: members whose phase A this item completed
     const int n = a.n, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nw = blockDim.x >> 5;
     const int bmax = nw * a.b_group;   // phase-B item: at most b_group atoms per warp
@@ -411,11 +419,13 @@ __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
             s_item[1] = ok ? ph : -1;
             s_item[2] = s;
             s_item[3] = e;
+            s_item[4] = c.merged;
         }
         __syncthreads();
         const int ell = (int)s_item[0];
         const int ph = (int)s_item[1];
         const long s = s_item[2], e = s_item[3];
+        const bool merged = s_item[4] != 0;
         if (ph < 0) return;
         // both branches end with a CTA barrier, after which thread 0 may rewrite s_item
         if (ph == 0) {
@@ -435,12 +445,41 @@ __device__ void fine_flow(const FineArgs& a, const SBShared<TJ>& sh) {
             if (s + warp < e) fine_phase_b<float>(a, s + warp, nw, e, ell, lane);
             __syncthreads();
         }
-        if (threadIdx.x == 0) {   // publish: the item's atoms per member
-            unsigned long long* done = ph == 0 ? doneA : doneB;
+        if (!merged) {
+            if (threadIdx.x == 0) {   // publish: the item's atoms per member
+                unsigned long long* done = ph == 0 ? doneA : doneB;
+                for (long p = s / n; p <= (e - 1) / n; ++p) {
+                    const long lo = p * n > s ? p * n : s, hi = (p + 1) * n < e ? (p + 1) * n : e;
+                    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> x(done[p]);
+                    x.fetch_add((unsigned long long)(hi - lo), cuda::memory_order_release);
+                }
+            }
+            continue;
+        }
+        // merged sub-step: publish the phase-A atoms; the CTA that completes a member (its count
+        // reaches (ell + 1) n, acquire: every batch of the member is visible) runs the member's
+        // phase B at once and publishes it
+        if (threadIdx.x == 0) {
+            int k = 0;
             for (long p = s / n; p <= (e - 1) / n; ++p) {
                 const long lo = p * n > s ? p * n : s, hi = (p + 1) * n < e ? (p + 1) * n : e;
-                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> x(done[p]);
-                x.fetch_add((unsigned long long)(hi - lo), cuda::memory_order_release);
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> x(doneA[p]);
+                const unsigned long long old = x.fetch_add((unsigned long long)(hi - lo), cuda::memory_order_acq_rel);
+                if (old + (unsigned long long)(hi - lo) == (unsigned long long)(ell + 1) * n) s_comp[1 + k++] = (int)p;
+            }
+            s_comp[0] = k;
+        }
+        __syncthreads();
+        const int ncomp = s_comp[0];
+        for (int c2 = 0; c2 < ncomp; ++c2) {
+            const long p = s_comp[1 + c2];
+            const long b0 = p * n, b1 = b0 + n;
+            for (long base = b0; base < b1; base += (long)nw * a.b_group)
+                if (base + warp < b1) fine_phase_b<float>(a, base + warp, nw, b1, ell, lane);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> x(doneB[p]);
+                x.fetch_add((unsigned long long)n, cuda::memory_order_release);
             }
         }
     }
@@ -489,6 +528,7 @@ static int launch_fine(pmd_engine* e, int nbatch, int n, double* q, double* v, l
     a.shape.rows4_atoms = e->tune.rows4_atoms;
     a.shape.noise_stage = e->tune.noise_stage;
     a.b_group = e->tune.b_group < 1 ? 1 : (e->tune.b_group > SB_B_GROUP_MAX ? SB_B_GROUP_MAX : e->tune.b_group);
+    a.merge_b = 1;
     a.pos = n <= PMD_POS_TABLE_MAX_ATOMS && sizeof(real) == 4 ? e->s_pos.as<unsigned char>() : nullptr;
     a.order = e->s_order.as<int>();
     a.Ls = e->s_order.as<int>() + e->cap_batch;

@@ -31,3 +31,21 @@ def test_binding_rejects_host_tensors():
     q = torch.as_tensor(sites)
     with pytest.raises(ValueError):
         P.sia_locate(q[None], q, q, box)
+
+
+def test_batch_means_interval():
+    """Batch means of residence times: every run is assigned to the block where it ends; with
+    identical blocks the interval collapses to zero, and with two regimes of different mean (a
+    slow switch) it is much wider than the per-exit interval, which ignores the correlation."""
+    from paper_2212_10508_gb300.residence import batch_means, mean_ci95
+    import numpy as np
+    L = [5, 5, 10] * 40                      # 120 runs, 800 frames, the same pattern everywhere
+    m, h, blocks = batch_means(L, 801, blocks=4)   # 800 frames of runs + the open last one
+    assert len(blocks) == 4 and h == 0.0 and m == np.mean(blocks)
+    rng = np.random.default_rng(1)
+    slow = list(rng.exponential(200, 60).astype(int) + 1)
+    fast = list(rng.exponential(50, 240).astype(int) + 1)
+    L2 = slow + fast
+    m2, h2, _ = batch_means(L2, int(np.sum(L2)) + 1, blocks=10)
+    _, hp = mean_ci95(L2)
+    assert h2 > 2 * hp
