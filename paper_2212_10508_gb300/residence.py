@@ -137,8 +137,9 @@ def main():
     ap.add_argument("--equil", type=int, default=2000)
     ap.add_argument("--delta-conv", type=float, default=1e-3)
     ap.add_argument("--delta-expl", type=float, default=0.1)
+    ap.add_argument("--seed", type=int, default=2212, help="master seed (displacements, velocities, noise)")
     a = ap.parse_args()
-    print(json.dumps(study(a.T, a.steps, a.window, a.equil, a.delta_conv, a.delta_expl)))
+    print(json.dumps(dict(study(a.T, a.steps, a.window, a.equil, a.delta_conv, a.delta_expl, seed=a.seed), seed=a.seed)))
 
 
 if __name__ == "__main__":
