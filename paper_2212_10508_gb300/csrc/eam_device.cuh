@@ -24,7 +24,7 @@ struct EamShared {
     double* F;                 // [3][n]
     double* dF;                // [n]
     unsigned short* nbl;       // Verlet list, EAM_LIST_CAP per atom, eam_pidx layout (nullptr: scan all atoms)
-    unsigned char* nbc;        // [n] list lengths
+    unsigned char* nbc;        // [S][n] lengths of the per-thread sub-lists (see eam_build_list)
     float4* qref;              // [n] wrapped positions at the last list build
     float4* pg;                // FP32 pair geometry (dx, dy, dz, r) of the density pass, EAM_PG_CAP per atom,
                                // eam_pidx layout
@@ -32,10 +32,14 @@ struct EamShared {
     unsigned char* pgc;        // [n][2] entries per thread slot, EAM_PG_FULL when a slot overflowed
 };
 
-// Verlet list of the one-CTA coarse path: every pair within max(d, c) + EAM_SKIN, in index
-// order, rebuilt when an atom has moved more than EAM_SKIN / 2 since the last build.  The pair
-// passes re-apply the exact cutoff test, so the list yields the same terms in the same order as
-// a scan over all atoms (bitwise the same sums).
+// Verlet list of the one-CTA coarse path: every pair within max(d, c) + EAM_SKIN, rebuilt when an
+// atom has moved more than EAM_SKIN / 2 since the last build.  With S threads per atom the list
+// is S sub-lists, one per thread: thread u of atom i gets the neighbours j with j mod S = u, in
+// index order (entry k of sub-list u in slot eam_pidx(i, k S + u, n, S)).  The pair passes
+// re-apply the exact cutoff test, so every thread sums the same terms in the same order whatever
+// the list's history (a list kept from earlier positions holds extra, rejected entries) and as a
+// scan over all atoms: C(x) is the same bits in the sweep, which keeps its list across intervals,
+// and in the batch, which builds a fresh one.
 constexpr int EAM_LIST_CAP = 64;
 constexpr float EAM_SKIN = 0.5f;
 
@@ -47,7 +51,7 @@ constexpr int EAM_PG_CAP = 24;
 constexpr unsigned char EAM_PG_FULL = 255;
 
 // Threads per atom in the pair passes of a CTA of blockDim.x threads: two when there are at least
-// 2n threads (thread u of atom i takes the pair entries u, u + 2, ...), one otherwise.
+// 2n threads (thread u of atom i takes the neighbours j with j mod 2 = u), one otherwise.
 __device__ __forceinline__ int eam_split(int n) { return (int)blockDim.x >= 2 * n ? 2 : 1; }
 
 // Slot of pair entry c of atom i in the list and the pair cache: [c / S][i][c % S], so that the
@@ -108,17 +112,18 @@ __device__ __forceinline__ void eam_build_list(const EamShared& s, int n, const 
                                                int* overflow) {
     const float boxf[3] = {(float)box[0], (float)box[1], (float)box[2]};
     const float ibf[3] = {1.0f / boxf[0], 1.0f / boxf[1], 1.0f / boxf[2]};
-    const int S = eam_split(n);
+    const int S = eam_split(n), cap = EAM_LIST_CAP / S;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const float4 qi = s.qf[i];
-        int c = 0;
+        int c[2] = {0, 0};
         for (int j = 0; j < n; ++j) {
             if (j == i || !(r2_f32(mi_f32(qi, s.qf[j], boxf, ibf)) < reach2)) continue;
-            if (c < EAM_LIST_CAP) s.nbl[eam_pidx(i, c, n, S)] = (unsigned short)j;
-            ++c;
+            const int u = S == 2 ? (j & 1) : 0;
+            if (c[u] < cap) s.nbl[eam_pidx(i, c[u] * S + u, n, S)] = (unsigned short)j;
+            ++c[u];
         }
-        if (c > EAM_LIST_CAP) atomicOr(overflow, 1);
-        s.nbc[i] = (unsigned char)(c > EAM_LIST_CAP ? EAM_LIST_CAP : c);
+        if (c[0] > cap || c[1] > cap) atomicOr(overflow, 1);
+        for (int u = 0; u < S; ++u) s.nbc[u * n + i] = (unsigned char)(c[u] > cap ? cap : c[u]);
         s.qref[i] = qi;
     }
 }
@@ -165,7 +170,7 @@ __device__ __forceinline__ void eam_forces_cta(const EamShared& s, int n, const 
     const bool list = s.nbl != nullptr;
     const bool cache = PGCACHE && sizeof(real) == 4 && s.pj != nullptr;
     // S threads per atom when the CTA has at least 2n threads (the launch shape decides; every
-    // coarse kernel uses the same one): thread u of atom i sums its pair entries u, u + S, ...,
+    // coarse kernel uses the same one): thread u of atom i sums over the neighbours j = u mod S,
     // and the two partial sums are combined by an xor-shuffle (symmetric: both threads hold the
     // same bits).  span covers whole warps so that every lane takes part in the shuffles.
     const int S = eam_split(n);
@@ -176,11 +181,12 @@ __device__ __forceinline__ void eam_forces_cta(const EamShared& s, int n, const 
         real rho = 0, ep = 0;
         if (act) {
             const float4 qi = s.qf[i];
-            const int cnt = list ? s.nbc[i] : n;
+            // this thread's neighbours j = u mod S: its sub-list, or every S-th atom without a list
+            const int cnt = list ? s.nbc[u * n + i] : (n - u + S - 1) / S;
             const int cap = EAM_PG_CAP / S, stride = S * n;
             int np = 0;
-            for (int c = u, o = i * S + u; c < cnt; c += S, o += stride) {   // o = eam_pidx(i, c, n, S)
-                const int j = list ? s.nbl[o] : c;
+            for (int k = 0, o = i * S + u; k < cnt; ++k, o += stride) {   // o = eam_pidx(i, k S + u, n, S)
+                const int j = list ? s.nbl[o] : k * S + u;
                 real dv[3], r;
                 if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
                 if constexpr (sizeof(real) == 4) {
@@ -226,9 +232,9 @@ __device__ __forceinline__ void eam_forces_cta(const EamShared& s, int n, const 
                 }
             } else {
                 const float4 qi = s.qf[i];
-                const int cnt = list ? s.nbc[i] : n;
-                for (int c = u, o = i * S + u; c < cnt; c += S, o += stride) {
-                    const int j = list ? s.nbl[o] : c;
+                const int cnt = list ? s.nbc[u * n + i] : (n - u + S - 1) / S;
+                for (int k = 0, o = i * S + u; k < cnt; ++k, o += stride) {
+                    const int j = list ? s.nbl[o] : k * S + u;
                     real dv[3], r;
                     if (!pair_in<real>(s, n, i, j, qi, box, boxf, ibf, p.screen2, r, dv)) continue;
                     eam_pair_force<real>(s, j, r, dv, dFi, d_, c_, c0, c1, c2, f0, f1, f2);

@@ -609,7 +609,7 @@ constexpr int EAM_PG_MAX_ATOMS = 256;     // ... and up to this size the FP32 pa
 
 __host__ __device__ inline size_t coarse_smem_bytes(int n, bool pg = true) {
     size_t b = (size_t)n * (3 * 8 + 16 + 3 * 8 + 8) + 64;
-    if (n <= EAM_LIST_MAX_ATOMS) b += (size_t)n * (EAM_LIST_CAP * 2 + 1 + 16) + 64;
+    if (n <= EAM_LIST_MAX_ATOMS) b += (size_t)n * (EAM_LIST_CAP * 2 + 2 + 16) + 64;
     if (pg && n <= EAM_PG_MAX_ATOMS) b += (size_t)n * (EAM_PG_CAP * (16 + 2) + 2) + 64;
     return (b + 15) / 16 * 16;
 }
@@ -633,7 +633,7 @@ __device__ inline EamShared coarse_carve(unsigned char* smem, int n, bool pg = t
     s.pj = nullptr;
     s.pgc = nullptr;
     if (pg && n <= EAM_PG_MAX_ATOMS) {
-        s.pg = reinterpret_cast<float4*>(align_up(reinterpret_cast<size_t>(s.nbc + n), 16));
+        s.pg = reinterpret_cast<float4*>(align_up(reinterpret_cast<size_t>(s.nbc + 2 * n), 16));
         s.pj = reinterpret_cast<unsigned short*>(s.pg + (size_t)n * EAM_PG_CAP);
         s.pgc = reinterpret_cast<unsigned char*>(s.pj + (size_t)n * EAM_PG_CAP);
     }
@@ -1070,6 +1070,12 @@ __global__ void __launch_bounds__(COARSE_MAX_THREADS, 1) k_parareal_sweep(int n,
     }
 }
 
+}  // namespace pmd
+
+#include "sweep_cluster.cuh"
+
+namespace pmd {
+
 // G_{l,n} for every interval n of a window, l = 0..L, all atoms: [count][L+1][3][natoms]
 __global__ void k_noise_window(uint64_t seed, int64_t n0, int count, int L1, int natoms, double* __restrict__ G) {
     const long total = (long)count * L1 * natoms;
@@ -1123,7 +1129,33 @@ int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, cons
         PMD_CUDA_TRY(cudaGetLastError());
         return PMD_OK;
     };
-    int rc = coarse_dispatch<SweepK>(e, n, kmax, go);
+    int rc;
+    if (e->p.coarse_kind == PMD_COARSE_FS && n >= 64 && n <= EAM_LIST_MAX_ATOMS) {
+        // the atoms of each interval spread over a cluster of up to 8 CTAs (SMs)
+        const int K = std::min(SWEEP_CLUSTER_MAX, (n + 31) / 32), m = (n + K - 1) / K;
+        const int S = n <= 256 ? 2 : 1, cthreads = std::max(32, (S * m + 31) / 32 * 32);
+        const size_t csm = sweep_cluster_smem_bytes(n, m, K);
+        const FSDev fs = make_fs(e->p.coarse);
+        auto kern = e->p.coarse.precision == PMD_FP64 ? k_parareal_sweep_cluster<double> : k_parareal_sweep_cluster<float>;
+        PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(K);
+        cfg.blockDim = dim3(cthreads);
+        cfg.dynamicSmemBytes = csm;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = K;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        PMD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, n, m, B[0], B[1], B[2], fs, Ld, L, n_in, n_fin, jumps, prev, cur,
+                                        cout, delta_expl, metric, (const double*)Gwin, res, e->status.as<int>()));
+        rc = PMD_OK;
+    } else {
+        rc = coarse_dispatch<SweepK>(e, n, kmax, go);
+    }
     if (rc) return rc;
     SweepResult* h = static_cast<SweepResult*>(e->pinned);
     PMD_CUDA_TRY(cudaMemcpyAsync(h, res, sizeof(SweepResult), cudaMemcpyDeviceToHost, st));

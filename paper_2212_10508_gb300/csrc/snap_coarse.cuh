@@ -199,9 +199,9 @@ __device__ void snap_coarse_forces_cta(const EamShared& s, const SnapCoarseShare
         cplx<real> acc[NH];
 #pragma unroll
         for (int e = 0; e < NH; ++e) acc[e] = {real(0), real(0)};
-        const int cnt = s.nbc[i];
-        for (int q = 0; q < cnt; ++q) {
-            const int j = s.nbl[eam_pidx(i, q, n, S)];
+        for (int u = 0, k = 0; u < S; k = 0, ++u)   // the S sub-lists in turn (see eam_build_list)
+        for (; k < s.nbc[u * n + i]; ++k) {
+            const int j = s.nbl[eam_pidx(i, k * S + u, n, S)];
             Vec4<real> dv;
             if (!snap_pair<real>(s, n, i, j, qi, box, boxf, ibf, c, dv)) continue;
             cplx<real> a, b;
@@ -236,9 +236,9 @@ __device__ void snap_coarse_forces_cta(const EamShared& s, const SnapCoarseShare
         cplx<real> ywi[4 * NH];
         snap_coarse_weights<real, TJ>(t.yh + (size_t)i * NH, ywi);
         double f[3] = {0.0, 0.0, 0.0};
-        const int cnt = s.nbc[i];
-        for (int q = 0; q < cnt; ++q) {
-            const int k = s.nbl[eam_pidx(i, q, n, S)];
+        for (int u = 0, kk = 0; u < S; kk = 0, ++u)   // the S sub-lists in turn
+        for (; kk < s.nbc[u * n + i]; ++kk) {
+            const int k = s.nbl[eam_pidx(i, kk * S + u, n, S)];
             Vec4<real> dv;
             if (!snap_pair<real>(s, n, i, k, qi, box, boxf, ibf, c, dv)) continue;
             real g[3], h[3];

@@ -145,3 +145,62 @@ def test_distributed_driver_with_engine_equals_single_gpu_driver():
     r = subprocess.run([sys.executable, "-c", DIST_WORKER.format(root=root, port=port)], env=env,
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]
+
+
+@pytest.mark.parametrize("ncell", [4, 5])                  # 129 atoms (5 CTAs), 251 atoms (8 CTAs)
+@pytest.mark.parametrize("precision", [P.FP64, P.FP32_BULK])
+@pytest.mark.parametrize("scheme,L", [(P.SCHEME_PAPER, 1), (P.SCHEME_PAPER, 3), (P.SCHEME_BAOAB, 2)])
+def test_cluster_sweep_equals_coarse_batch(ncell, precision, scheme, L):
+    """The correction sweep of the Finnis-Sinclair coarse potential runs on a cluster of CTAs for
+    systems of 64..512 atoms; the coarse states it caches, C(cur_n), must equal bit for bit those
+    of the one-CTA coarse batch kernel applied to the same cur_n (the jumps J_n = F - C(prev_n) of
+    the next iteration use the batch's values), and without jumps cur_{n+1} = C(cur_n)."""
+    pos, box = W.bcc_sia(ncell)
+    n = pos.shape[1]
+    N = 7
+    eng = P.Engine(n, box, P.snap_params(), P.fs_params(precision=precision))
+    lp = P.langevin(dt=2e-3, gamma=1.0, T=2000.0, scheme=scheme, seed=23)
+    cur = torch.zeros(N + 1, 6, n, dtype=torch.float64, device=dev())
+    cur[0, :3] = T(W.displaced(pos, 0.05, W.rng(24, 1)))
+    cur[0, 3:] = T(W.velocities(n, 2000.0, W.rng(24, 2)))
+    cache = torch.zeros(N, 6, n, dtype=torch.float64, device=dev())
+    delta, n_stop = eng.parareal_correct(0, N, None, cur, cur, cache, float("inf"), P.METRIC_MAXDISP, L, lp)
+    eng.sync_status()
+    assert n_stop == N
+    batch = cur[:N].clone()
+    eng.baoab_propagate_batch(P.COARSE, batch, None, T(np.full(N, L, np.int32), torch.int32),
+                              T(np.arange(N), torch.int64), lp)
+    eng.sync_status()
+    assert torch.equal(batch, cache)
+    assert torch.equal(cur[1:], cache)
+
+
+def test_cluster_sweep_adaptive_parareal_matches_algorithm_2_251_atoms():
+    """Algorithm 2 on the 251-atom cell (cluster sweep) against the oracle's transcription:
+    the same slabs and iteration counts, trajectories to 1e-8 Angstrom."""
+    pos, box = W.bcc_sia(5)
+    n = pos.shape[1]
+    q0 = W.displaced(pos, 0.05, W.rng(25, 1))
+    v0 = W.velocities(n, 1500.0, W.rng(25, 2))
+    beta = W.fitted_beta()
+    eng = P.Engine(n, box, P.snap_params(), P.fs_params(), beta=T(beta))
+    Nint, L, dc, de = 6, 1, 1e-10, 2e-3
+    lp = P.langevin(dt=DT, gamma=GAMMA, T=1500.0, seed=SEED, schedule=P.SCHED_ROBUST)
+    cur, st = P.adaptive_parareal(eng, T(q0), T(v0), Nint, L, dc, de, lp, metric=P.METRIC_MAXDISP)
+    eng.sync_status()
+    olp = O.langevin(dt=DT, gamma=GAMMA, T=1500.0, seed=SEED, schedule=O.SCHED_ROBUST)
+
+    def make(pot):
+        def prop(states, ns):
+            q = np.ascontiguousarray(np.array([s[0] for s in states]))
+            v = np.ascontiguousarray(np.array([s[1] for s in states]))
+            O.propagate(pot, q, v, box, [L] * len(ns), ns, olp)
+            return [(q[i], v[i]) for i in range(len(ns))]
+        return prop
+    ocur, olog = PR.adaptive(q0, v0, Nint, dc, de, make(O.potential(O.POT_SNAP, beta=beta)), make(O.potential(O.POT_FS)),
+                             metric="maxdisp")
+    want = [(w["n_init"], e, k, i) for i, w in enumerate(olog.windows) for e, k in w["subs"]]
+    assert st.log() == want
+    g = N(cur)
+    for k in range(Nint + 1):
+        assert np.abs(g[k, :3] - ocur[k][0]).max() < 1e-8
