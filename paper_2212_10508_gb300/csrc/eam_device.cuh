@@ -63,13 +63,15 @@ __device__ __forceinline__ int eam_pidx(int i, int c, int n, int S) {
 }
 
 // Position wrapped to [0, L) per axis (up to rounding) as FP32: x - L floor(x / L), with the
-// quotient taken as x * (1/L) (the reciprocals are loop invariants of every caller).
+// quotient taken as x * (1/L), iL = 1/L (the reciprocals are loop invariants of every caller).
+// wrap1_f32 is one coordinate; wrap_f32 the three, with the same operations.
+__device__ __forceinline__ float wrap1_f32(double x, double L, double iL) {
+    x -= L * floor(x * iL);
+    return (float)x;
+}
 __device__ __forceinline__ float4 wrap_f32(double x, double y, double z, const double box[3]) {
-    const double i0 = 1.0 / box[0], i1 = 1.0 / box[1], i2 = 1.0 / box[2];
-    x -= box[0] * floor(x * i0);
-    y -= box[1] * floor(y * i1);
-    z -= box[2] * floor(z * i2);
-    return make_float4((float)x, (float)y, (float)z, 0.f);
+    return make_float4(wrap1_f32(x, box[0], 1.0 / box[0]), wrap1_f32(y, box[1], 1.0 / box[1]),
+                       wrap1_f32(z, box[2], 1.0 / box[2]), 0.f);
 }
 
 // FP32 minimum-image displacement b - a (ibf: reciprocal box lengths; the image only differs
@@ -141,15 +143,28 @@ __device__ __forceinline__ int eam_list_stale(const EamShared& s, int n, const d
     return __syncthreads_or(stale);
 }
 
-// Force term of pair (i, j) at distance r, displacement dv = r_j - r_i, added to f
+// Pair (i, j) at distance r: g = (dE/dr) / r, the factor of the force g (r_j - r_i) on atom i, from
+// the pair term and the embedding derivatives F'(rho_i) = dFi and F'(rho_j); false when r is beyond
+// both the density and the pair range (no force).
+template <typename real>
+__device__ __forceinline__ bool eam_pair_g(real r, real dFi, real dFj, real d_, real c_, real c0, real c1, real c2,
+                                           real& g) {
+    real dEdr = real(0);
+    if (r < d_) dEdr += (dFi + dFj) * real(2) * (r - d_);
+    if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
+    if (r < d_ || r < c_) {
+        g = dEdr / r;
+        return true;
+    }
+    return false;
+}
+
+// Adds the pair's force on atom i, g (r_j - r_i), to (f0, f1, f2) (nothing outside both ranges).
 template <typename real>
 __device__ __forceinline__ void eam_pair_force(const EamShared& s, int j, real r, const real dv[3], real dFi, real d_,
                                                real c_, real c0, real c1, real c2, real& f0, real& f1, real& f2) {
-    real dEdr = real(0);
-    if (r < d_) dEdr += (dFi + (real)s.dF[j]) * real(2) * (r - d_);
-    if (r < c_) dEdr += real(2) * (r - c_) * (c0 + c1 * r + c2 * r * r) + (r - c_) * (r - c_) * (c1 + real(2) * c2 * r);
-    if (r < d_ || r < c_) {
-        const real g = dEdr / r;
+    real g;
+    if (eam_pair_g<real>(r, dFi, (real)s.dF[j], d_, c_, c0, c1, c2, g)) {
         f0 += g * dv[0];
         f1 += g * dv[1];
         f2 += g * dv[2];

@@ -18,11 +18,11 @@ struct LangevinDev {
     uint64_t seed;
 };
 
+// (selects rather than an indexed load, so that a kernel-parameter copy of L needs no local memory)
 __device__ __forceinline__ double sched_sigma(const LangevinDev& L, int ell) {
-    int C = 1;
-    if (L.schedule == PMD_SCHED_ROBUST) C = ell == 0 ? 3 : 1;
-    else if (L.schedule == PMD_SCHED_L1_SYM) C = 2;
-    return L.sig[C];
+    if (L.schedule == PMD_SCHED_ROBUST) return ell == 0 ? L.sig[3] : L.sig[1];
+    if (L.schedule == PMD_SCHED_L1_SYM) return L.sig[2];
+    return L.sig[1];
 }
 
 // half kick: base + dt/2 a - dt/2 gamma vdamp + s G
