@@ -587,6 +587,7 @@ def run_ours(args):
     if rank == 0 and not args.no_parareal:   # one-GPU extras run on rank 0 only
         out["parareal"] = _parareal(P, W, dev, torch)                              # one window of 300
         out["parareal_windows_100"] = _parareal(P, W, dev, torch, window=100)     # three windows of 100
+        out["parareal_windows_1000"] = _parareal(P, W, dev, torch, Nh=1000, window=1000)   # one window of 1000
 
     # ---- matched force error FP32-bulk vs FP64 and the plain-FP64 form on the same workload
     s64 = P.Snap(P.snap_params(precision=P.FP64))
