@@ -1133,11 +1133,11 @@ int parareal_sweep(pmd_engine* e, int n_in, int n_fin, const double* jumps, cons
     if (e->p.coarse_kind == PMD_COARSE_FS && n >= 64 && n <= EAM_LIST_MAX_ATOMS) {
         // the atoms of each interval spread over a cluster of up to 8 CTAs (SMs)
         const int K = std::min(SWEEP_CLUSTER_MAX, (n + 31) / 32), m = (n + K - 1) / K;
-        // threads: S SC_W per own atom in the pair passes, and three warps per 32 own atoms (the
-        // axis split of the integrator); at most 256
-        const int S = n <= 256 ? 2 : 1;
-        const int cthreads = std::max((S * SC_W * m + 31) / 32 * 32, 96 * ((m + 31) / 32));
-        const size_t csm = sweep_cluster_smem_bytes(n, m, K, S, e->p.coarse.precision == PMD_FP64 ? 8 : 4);
+        // threads: S W per own atom in the pair passes, and three warps per 32 own atoms (the
+        // axis split of the integrator); at most 512
+        const int S = n <= 256 ? 2 : 1, rb = e->p.coarse.precision == PMD_FP64 ? 8 : 4;
+        const int cthreads = std::max((S * sc_workers(rb) * m + 31) / 32 * 32, 96 * ((m + 31) / 32));
+        const size_t csm = sweep_cluster_smem_bytes(n, m, K, S, rb);
         const FSDev fs = make_fs(e->p.coarse);
         auto kern = e->p.coarse.precision == PMD_FP64 ? k_parareal_sweep_cluster<double> : k_parareal_sweep_cluster<float>;
         PMD_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csm));

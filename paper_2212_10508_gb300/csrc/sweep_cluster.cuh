@@ -35,7 +35,9 @@
 namespace pmd {
 
 constexpr int SWEEP_CLUSTER_MAX = 8;   // portable cluster size
-constexpr int SC_W = 4;                // worker threads per sub-list in the pair passes and the list build
+// Worker threads per sub-list in the pair passes and the list build: 8 in FP32-bulk mode, 4 in
+// FP64 mode (whose pair geometry is FP64: more warps only queue on the FP64 units).
+__host__ __device__ constexpr int sc_workers(int real_bytes) { return real_bytes == 4 ? 8 : 4; }
 
 // Per-entry terms of the pair passes: the density pass's workers store the pair geometry
 // (r, r_j - r_i), r = +inf for an entry outside the screen radius; the force pass's workers
@@ -112,15 +114,15 @@ __device__ inline SweepClusterShared sweep_cluster_carve(unsigned char* smem, in
 }
 
 // The cluster's view: rank, owned atoms, the S sub-lists of an atom (the one-CTA kernels' split of
-// its pairs) and the T = S SC_W threads of an atom in the pair passes: thread t of the CTA works
-// for own atom t / T, sub-list (t / SC_W) mod S, as worker t mod SC_W.
+// its pairs) and the T = S W threads of an atom in the pair passes: thread t of the CTA works for
+// own atom t / T, sub-list (t / W) mod S, as worker t mod W.
 struct SweepOwn {
-    int K, rank, a0, mown, m, S, T;
+    int K, rank, a0, mown, m, S, W, T;
 };
 
 // Own atoms' Verlet lists: the sub-lists of eam_build_list (sub-list u of an atom holds the pairs
 // within the reach with neighbour index j = u mod S, in index order) over the m own slots.  The
-// SC_W workers of a sub-list scan consecutive chunks of its candidates j, count their hits, take
+// W workers of a sub-list scan consecutive chunks of its candidates j, count their hits, take
 // their offsets from a prefix sum over the workers (shuffles) and write their hits in a second
 // scan, so the sub-list comes out in index order.
 __device__ __forceinline__ void sc_build_lists(const SweepClusterShared& s, const SweepOwn& w, int n, const double box[3],
@@ -130,10 +132,10 @@ __device__ __forceinline__ void sc_build_lists(const SweepClusterShared& s, cons
     const int S = w.S, cap = EAM_LIST_CAP / S;
     const int span = (w.T * w.m + 31) / 32 * 32;
     for (int t = threadIdx.x; t < span; t += blockDim.x) {   // whole warps: the shuffles take every lane
-        const int li = t / w.T, u = (t / SC_W) % S, v = t % SC_W, i = w.a0 + li;
+        const int li = t / w.T, u = (t / w.W) % S, v = t % w.W, i = w.a0 + li;
         const bool act = li < w.mown;
         const int ncls = act ? (n - u + S - 1) / S : 0;   // candidates j = u + S c, c < ncls
-        const int per = (ncls + SC_W - 1) / SC_W;
+        const int per = (ncls + w.W - 1) / w.W;
         const int c0 = v * per, c1 = c0 + per < ncls ? c0 + per : ncls;
         const float4 qi = act ? s.qf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         int hits = 0;
@@ -143,11 +145,11 @@ __device__ __forceinline__ void sc_build_lists(const SweepClusterShared& s, cons
             hits += j != i && r2_f32(mi_f32(qi, s.qf[j], boxf, ibf)) < reach2;
         }
         int incl = hits;   // inclusive prefix over the workers of this sub-list
-        for (int d = 1; d < SC_W; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, d, SC_W);
+        for (int d = 1; d < w.W; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d, w.W);
             if (v >= d) incl += y;
         }
-        const int total = __shfl_sync(0xffffffffu, incl, SC_W - 1, SC_W);
+        const int total = __shfl_sync(0xffffffffu, incl, w.W - 1, w.W);
         int k = incl - hits;
         for (int c = c0; c < c1 && k < cap; ++c) {
             const int j = u + S * c;
@@ -165,7 +167,7 @@ __device__ __forceinline__ void sc_build_lists(const SweepClusterShared& s, cons
 
 // The two EAM pair passes of the own atoms, with the sums of the one-CTA kernels (eam_forces_cta):
 // per sub-list, the terms of its entries added in entry order, then the S sub-lists' sums combined
-// by an xor-shuffle.  The SC_W workers of a sub-list take entries v, v + SC_W, ...: in the density
+// by an xor-shuffle.  The W workers of a sub-list take entries v, v + W, ...: in the density
 // pass they store each entry's pair geometry in the term array (the force pass reuses it, as the
 // one-CTA kernels' pair cache does, with the same bits); in the force pass they compute g from it
 // and F'(rho_j).  After a warp barrier the sub-list's first worker adds the terms in order with
@@ -185,13 +187,13 @@ __device__ __forceinline__ void sc_forces(const SweepClusterShared& s, const Swe
     const int S = w.S, pitch = sc_term_pitch(S);
     const int span = (w.T * w.m + 31) / 32 * 32;
     for (int t = threadIdx.x; t < span; t += blockDim.x) {
-        const int li = t / w.T, u = (t / SC_W) % S, v = t % SC_W, i = w.a0 + li;
+        const int li = t / w.T, u = (t / w.W) % S, v = t % w.W, i = w.a0 + li;
         const bool act = li < w.mown;
         const int cnt = act ? s.nbc[u * w.m + li] : 0;
         ScTerm<real>* tr = reinterpret_cast<ScTerm<real>*>(s.term) + (size_t)(li * S + u) * pitch;
         const float4 qi = act ? s.qf[i] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 2
-        for (int k = v; k < cnt; k += SC_W) {
+        for (int k = v; k < cnt; k += w.W) {
             const int j = s.nbl[eam_pidx(li, k * S + u, w.m, S)];
             real dv[3], r;
             ScTerm<real> y{real(INFINITY), 0, 0, 0};
@@ -207,7 +209,7 @@ __device__ __forceinline__ void sc_forces(const SweepClusterShared& s, const Swe
                 const real x = r < d_ ? r - d_ : real(0);
                 rho += x * x;
             }
-        if (S == 2) rho += __shfl_xor_sync(0xffffffffu, rho, SC_W);
+        if (S == 2) rho += __shfl_xor_sync(0xffffffffu, rho, w.W);
         if (act && u == 0 && v == 0) {
             if constexpr (sizeof(real) == 4) {   // the value the one-CTA kernels store as a double
                 const float dF = rho > 0.f ? -0.5f * (float)p.A / sqrtf(rho) : 0.0f;
@@ -220,7 +222,7 @@ __device__ __forceinline__ void sc_forces(const SweepClusterShared& s, const Swe
     }
     cl.sync();   // every CTA has every F'(rho); the density terms are read
     for (int t = threadIdx.x; t < span; t += blockDim.x) {
-        const int li = t / w.T, u = (t / SC_W) % S, v = t % SC_W, i = w.a0 + li;
+        const int li = t / w.T, u = (t / w.W) % S, v = t % w.W, i = w.a0 + li;
         const bool act = li < w.mown;
         const int cnt = act ? s.nbc[u * w.m + li] : 0;
         ScTerm<real>* tr = reinterpret_cast<ScTerm<real>*>(s.term) + (size_t)(li * S + u) * pitch;
@@ -229,7 +231,7 @@ __device__ __forceinline__ void sc_forces(const SweepClusterShared& s, const Swe
         else dFr = s.dF;
         const real dFi = act ? dFr[i] : real(0);
 #pragma unroll 2
-        for (int k = v; k < cnt; k += SC_W) {
+        for (int k = v; k < cnt; k += w.W) {
             const int j = s.nbl[eam_pidx(li, k * S + u, w.m, S)];
             const ScTerm<real> gm = tr[k];
             real g;
@@ -249,9 +251,9 @@ __device__ __forceinline__ void sc_forces(const SweepClusterShared& s, const Swe
                 f2 += y.x * y.w;
             }
         if (S == 2) {
-            f0 += __shfl_xor_sync(0xffffffffu, f0, SC_W);
-            f1 += __shfl_xor_sync(0xffffffffu, f1, SC_W);
-            f2 += __shfl_xor_sync(0xffffffffu, f2, SC_W);
+            f0 += __shfl_xor_sync(0xffffffffu, f0, w.W);
+            f1 += __shfl_xor_sync(0xffffffffu, f1, w.W);
+            f2 += __shfl_xor_sync(0xffffffffu, f2, w.W);
         }
         if (act && u == 0 && v == 0) {
             s.F[li] = (double)f0;
@@ -397,7 +399,7 @@ __device__ __forceinline__ void sc_totals(const SweepClusterShared& s, const Swe
 }
 
 template <typename real>
-__global__ void __launch_bounds__(256, 1) k_parareal_sweep_cluster(
+__global__ void __launch_bounds__(512, 1) k_parareal_sweep_cluster(
     int n, int m, double b0, double b1, double b2, FSDev fs, LangevinDev L, int nsteps, int n_in, int n_fin,
     const double* __restrict__ jumps, const double* __restrict__ prev, double* __restrict__ cur,
     double* __restrict__ cout, double delta_expl, int metric, const double* __restrict__ Gwin, SweepResult* res,
@@ -414,7 +416,8 @@ __global__ void __launch_bounds__(256, 1) k_parareal_sweep_cluster(
     w.a0 = w.rank * m;
     w.mown = w.a0 >= n ? 0 : (n - w.a0 < m ? n - w.a0 : m);
     w.S = n <= 256 ? 2 : 1;   // the entry split of the one-CTA kernels' launch shape
-    w.T = w.S * SC_W;
+    w.W = sc_workers((int)sizeof(real));
+    w.T = w.S * w.W;
     SweepClusterShared s = sweep_cluster_carve(smem, n, m, w.K, w.S, (int)sizeof(real));
     int cb = 0;   // current position buffer (the same in every CTA: all publish at the same points)
     const double box[3] = {b0, b1, b2};
