@@ -147,15 +147,29 @@ def test_distributed_driver_with_engine_equals_single_gpu_driver():
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]
 
 
-@pytest.mark.parametrize("ncell", [4, 5])                  # 129 atoms (5 CTAs), 251 atoms (8 CTAs)
+def _sweep_system(name):
+    """Cells of the cluster sweep's range: K = min(8, ceil(n/32)) CTAs of m = ceil(n/K) own atoms,
+    two threads per atom's pairs up to 256 atoms, one above."""
+    if name == "first65":   # 65 atoms of the 129-atom cell: 3 CTAs of 22, 22, 21 atoms
+        pos, box = W.bcc_sia(4)
+        return np.ascontiguousarray(pos[:, :65]), box
+    return W.bcc_sia({"129": 4, "251": 5, "433": 6}[name])
+
+
+@pytest.mark.parametrize("system", ["first65", "129", "251", "433"])
 @pytest.mark.parametrize("precision", [P.FP64, P.FP32_BULK])
 @pytest.mark.parametrize("scheme,L", [(P.SCHEME_PAPER, 1), (P.SCHEME_PAPER, 3), (P.SCHEME_BAOAB, 2)])
-def test_cluster_sweep_equals_coarse_batch(ncell, precision, scheme, L):
+@pytest.mark.parametrize("jumps", [False, True])
+def test_cluster_sweep_equals_coarse_batch(system, precision, scheme, L, jumps):
     """The correction sweep of the Finnis-Sinclair coarse potential runs on a cluster of CTAs for
     systems of 64..512 atoms; the coarse states it caches, C(cur_n), must equal bit for bit those
     of the one-CTA coarse batch kernel applied to the same cur_n (the jumps J_n = F - C(prev_n) of
-    the next iteration use the batch's values), and without jumps cur_{n+1} = C(cur_n)."""
-    pos, box = W.bcc_sia(ncell)
+    the next iteration use the batch's values), with or without jumps (a jump moves every atom,
+    so the sweep's Verlet lists and the batch's come from different position histories), and
+    without jumps cur_{n+1} = C(cur_n).  The systems cover an uneven split over 3 CTAs, 5 and 8
+    CTAs with two threads per atom, and 8 CTAs of 55 atoms with one thread per atom (own atoms in
+    two blocks of 32)."""
+    pos, box = _sweep_system(system)
     n = pos.shape[1]
     N = 7
     eng = P.Engine(n, box, P.snap_params(), P.fs_params(precision=precision))
@@ -163,8 +177,13 @@ def test_cluster_sweep_equals_coarse_batch(ncell, precision, scheme, L):
     cur = torch.zeros(N + 1, 6, n, dtype=torch.float64, device=dev())
     cur[0, :3] = T(W.displaced(pos, 0.05, W.rng(24, 1)))
     cur[0, 3:] = T(W.velocities(n, 2000.0, W.rng(24, 2)))
+    J = None
+    if jumps:
+        g = W.rng(24, 3)
+        J = T(np.concatenate([g.normal(0.0, 0.02, (N, 3, n)), g.normal(0.0, 0.5, (N, 3, n))], axis=1))
+    prev = cur.clone()
     cache = torch.zeros(N, 6, n, dtype=torch.float64, device=dev())
-    delta, n_stop = eng.parareal_correct(0, N, None, cur, cur, cache, float("inf"), P.METRIC_MAXDISP, L, lp)
+    delta, n_stop = eng.parareal_correct(0, N, J, prev, cur, cache, float("inf"), P.METRIC_MAXDISP, L, lp)
     eng.sync_status()
     assert n_stop == N
     batch = cur[:N].clone()
@@ -172,7 +191,10 @@ def test_cluster_sweep_equals_coarse_batch(ncell, precision, scheme, L):
                               T(np.arange(N), torch.int64), lp)
     eng.sync_status()
     assert torch.equal(batch, cache)
-    assert torch.equal(cur[1:], cache)
+    if jumps:
+        assert torch.equal(cur[1:], cache + J)
+    else:
+        assert torch.equal(cur[1:], cache)
 
 
 def test_cluster_sweep_adaptive_parareal_matches_algorithm_2_251_atoms():
