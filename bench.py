@@ -41,7 +41,7 @@ WORKLOAD3 = ("2001-atom W+SIA cell (10^3 cells), SNAP 2J=8 fitted, 32 intervals 
 # capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (fingerprint of the persistent kernel's translation unit and of
 # the host code that builds its tables); reported as null otherwise.
-TRAFFIC = {"bytes_per_launch": 3.30e6 + 19.80e6, "csrc_sha256_16": "62c503c9c562f0e7"}
+TRAFFIC = {"bytes_per_launch": 3.30e6 + 19.80e6, "csrc_sha256_16": "9194d0d27a0ea418"}
 # CPU-baseline samples of the oracle: (intervals or members, steps each) of config 2 and config 3,
 # on all host cores; the single-thread legs take one interval or member of the same sample (the
 # oracle's per-atom-step cost on one thread does not depend on how many members a call holds)
@@ -49,8 +49,11 @@ CPU_SAMPLES = {"cfg2": (8, 100), "cfg3": (2, 20)}
 CPU_SAMPLES_1T = {"cfg2": (1, 100), "cfg3": (1, 10)}
 
 
-KERNEL_SOURCES = ("propagate.cu", "snap.cu", "snap_launch.cuh", "snap_kernels.cuh", "snap_batch.cuh", "snap_v2.cuh", "snap_device.cuh",
-                  "device_common.cuh", "langevin_device.cuh", "eam_device.cuh", "pmd_internal.h", "status_bits.h")
+# the persistent kernel's translation unit (propagate.cu and every header it includes) and the host
+# code that builds its tables (snap.cu)
+KERNEL_SOURCES = ("propagate.cu", "snap.cu", "snap_kernels.cuh", "snap_batch.cuh", "snap_v2.cuh", "snap_device.cuh",
+                  "device_common.cuh", "langevin_device.cuh", "eam_device.cuh", "snap_coarse.cuh", "sweep_cluster.cuh",
+                  "pmd_internal.h", "status_bits.h")
 
 
 def _csrc_fingerprint():
@@ -329,6 +332,32 @@ def _parareal(P, W, dev, torch, Nh=300, window=300, ncell=5, T=1500.0):
             "final_max_dq_vs_sequential_A": float((qend - ref[0, :3]).abs().max().item())}
 
 
+def _energy_path(P, torch, tq, box, tbeta, snaps, reps=5):
+    """SNAP energies and dE/dbeta without forces (U_tot pass, bispectrum B, energy sums: the path of
+    the autograd forward and of the beta-fit design rows) on the batch's start states, per
+    precision: CUDA-event time per call on the current stream after one warm-up call, and the
+    bispectrum's algorithmic flops (34 946 Clebsch-Gordan terms x 8 flop per atom at 2J = 8) over
+    that time, a lower bound of the path's flop rate (the U pass is not counted)."""
+    nb, _, n = tq.shape
+    out = {"workload": "%d x %d-atom W+SIA start states of the batch, 2J = 8, energies + dE/dbeta" % (nb, n)}
+    for name, s in snaps:
+        P.snap_energy_forces(s, tq, box, tbeta, energy=True, forces=False, sumB=True)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            P.snap_energy_forces(s, tq, box, tbeta, energy=True, forces=False, sumB=True)
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        s.sync_status()
+        t = float(np.median(ms))
+        out[name] = {"ms_per_call": round(t, 3), "atoms_per_s": nb * n / (t / 1e3),
+                     "bispectrum_tflops_lower_bound": round(nb * n * 34946 * 8 / (t / 1e3) / 1e12, 3)}
+    return out
+
+
 def _roofline(flops, k_ms, peak_tf, basis, kernel, measured=None, traffic=None):
     achieved = flops / (k_ms / 1e3) / 1e12
     r = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tf, 2), "unit": "TFLOP/s",
@@ -596,6 +625,8 @@ def run_ours(args):
     _, F32, _ = P.snap_energy_forces(s32, tq, box, tbeta)
     ferr = float(((F32 - F64).abs().max() / F64.abs().max()).item())
     out["fp32_force_rel_err_vs_fp64"] = ferr
+    if rank == 0:
+        out["energy_path"] = _energy_path(P, torch, tq, box, tbeta, (("fp32_bulk", s32), ("fp64", s64)))
     if rank == 0 and not args.no_fp64:
         e64 = P.Engine(n, box, P.snap_params(precision=P.FP64), P.fs_params(), beta=tbeta)
         e64.reserve(NSLAB)

@@ -73,8 +73,9 @@ typedef struct {
     double rfac0;     /* in (0, 1] */
     double rmin0;     /* must be 0 */
     int switchflag;   /* 1: weights fc(r); 0: weights 1 */
-    int precision;    /* PMD_FP64, or PMD_FP32_BULK: U/Z/Y arithmetic in FP32, bispectrum,
-                         energy and force sums in FP64 */
+    int precision;    /* PMD_FP64, or PMD_FP32_BULK: U/Z/Y arithmetic in FP32 (the bispectrum's
+                         Z elements included), the bispectrum's sum over elements, energy and
+                         force sums in FP64 */
 } pmd_snap_params;
 
 /* Finnis-Sinclair EAM (Sec. 3.1; the coarse potential V_C):

@@ -71,7 +71,10 @@ static __global__ void __launch_bounds__(snap_cta_threads<real, TJ>(), 1)
 
 // B_t of one atom from U_tot (full layout): Re sum_{m m'} conj(U^j) Z^j_{j1 j2}, FP64 accumulation.
 // Thread (t, atom), triple-major: the 32 lanes of a warp take 32 atoms of the same triple, so every
-// loop bound and Clebsch-Gordan index is warp-uniform.
+// loop bound and Clebsch-Gordan index is warp-uniform.  FP64 mode: every operation in FP64.
+// FP32-bulk mode: each element Z(m, m') (a Clebsch-Gordan double sum of at most (j1+1)^2 products)
+// in FP32, the sum of conj(U) Z over the elements in FP64 -- FP32 arithmetic with FP64
+// accumulation of B (an FP64 instruction costs as much as dozens of FP32 ones on this part).
 template <typename real, int TJ>
 static __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, long natoms_all, int nB,
                                   const int4* __restrict__ triblk, const real* __restrict__ cg,
@@ -90,24 +93,44 @@ static __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, lo
     const cplx<real>* Uj = U + f_off(tj);
     const int s = (ta + tbb - tj) / 2;
     double B = 0.0;
-    for (int p = 0; p <= tj; ++p)
-        for (int q = 0; q <= tj; ++q) {
-            double zr = 0, zi = 0;
-            for (int p1 = max(0, p + s - tbb); p1 <= min(ta, p + s); ++p1) {
-                const int p2 = p + s - p1;
-                const double c1 = (double)c[p1 * (tbb + 1) + p2];
-                for (int q1 = max(0, q + s - tbb); q1 <= min(ta, q + s); ++q1) {
-                    const int q2 = q + s - q1;
-                    const double cc = c1 * (double)c[q1 * (tbb + 1) + q2];
-                    const cplx<real> x = Ua[p1 * (ta + 1) + q1], y = Ub[p2 * (tbb + 1) + q2];
-                    const double xr = x.re, xi = x.im, yr = y.re, yi = y.im;
-                    zr += cc * (xr * yr - xi * yi);
-                    zi += cc * (xr * yi + xi * yr);
+    if constexpr (sizeof(real) == 4) {
+        for (int p = 0; p <= tj; ++p)
+            for (int q = 0; q <= tj; ++q) {
+                float zr = 0.f, zi = 0.f;
+                for (int p1 = max(0, p + s - tbb); p1 <= min(ta, p + s); ++p1) {
+                    const int p2 = p + s - p1;
+                    const float c1 = c[p1 * (tbb + 1) + p2];
+                    for (int q1 = max(0, q + s - tbb); q1 <= min(ta, q + s); ++q1) {
+                        const int q2 = q + s - q1;
+                        const float cc = c1 * c[q1 * (tbb + 1) + q2];
+                        const cplx<real> x = Ua[p1 * (ta + 1) + q1], y = Ub[p2 * (tbb + 1) + q2];
+                        zr = fmaf(cc, x.re * y.re - x.im * y.im, zr);
+                        zi = fmaf(cc, x.re * y.im + x.im * y.re, zi);
+                    }
                 }
+                const cplx<real> u = Uj[p * (tj + 1) + q];
+                B += (double)(u.re * zr) + (double)(u.im * zi);
             }
-            const cplx<real> u = Uj[p * (tj + 1) + q];
-            B += (double)u.re * zr + (double)u.im * zi;
-        }
+    } else {
+        for (int p = 0; p <= tj; ++p)
+            for (int q = 0; q <= tj; ++q) {
+                double zr = 0, zi = 0;
+                for (int p1 = max(0, p + s - tbb); p1 <= min(ta, p + s); ++p1) {
+                    const int p2 = p + s - p1;
+                    const double c1 = (double)c[p1 * (tbb + 1) + p2];
+                    for (int q1 = max(0, q + s - tbb); q1 <= min(ta, q + s); ++q1) {
+                        const int q2 = q + s - q1;
+                        const double cc = c1 * (double)c[q1 * (tbb + 1) + q2];
+                        const cplx<real> x = Ua[p1 * (ta + 1) + q1], y = Ub[p2 * (tbb + 1) + q2];
+                        const double xr = x.re, xi = x.im, yr = y.re, yi = y.im;
+                        zr += cc * (xr * yr - xi * yi);
+                        zi += cc * (xr * yi + xi * yr);
+                    }
+                }
+                const cplx<real> u = Uj[p * (tj + 1) + q];
+                B += (double)u.re * zr + (double)u.im * zi;
+            }
+    }
     Bout[ia * nB + t] = B;
 }
 
