@@ -74,8 +74,8 @@ typedef struct {
     double rmin0;     /* must be 0 */
     int switchflag;   /* 1: weights fc(r); 0: weights 1 */
     int precision;    /* PMD_FP64, or PMD_FP32_BULK: U/Z/Y arithmetic in FP32 (the bispectrum's
-                         Z elements included), the bispectrum's sum over elements, energy and
-                         force sums in FP64 */
+                         Z elements included), the bispectrum's sum over elements and the force
+                         sums in double-float (FP64-class), energy sums in FP64 */
 } pmd_snap_params;
 
 /* Finnis-Sinclair EAM (Sec. 3.1; the coarse potential V_C):

@@ -73,8 +73,9 @@ static __global__ void __launch_bounds__(snap_cta_threads<real, TJ>(), 1)
 // Thread (t, atom), triple-major: the 32 lanes of a warp take 32 atoms of the same triple, so every
 // loop bound and Clebsch-Gordan index is warp-uniform.  FP64 mode: every operation in FP64.
 // FP32-bulk mode: each element Z(m, m') (a Clebsch-Gordan double sum of at most (j1+1)^2 products)
-// in FP32, the sum of conj(U) Z over the elements in FP64 -- FP32 arithmetic with FP64
-// accumulation of B (an FP64 instruction costs as much as dozens of FP32 ones on this part).
+// in FP32, and the sum of conj(U) Z over the elements in double-float arithmetic (FP64-class
+// accuracy on the FP32 pipes; an FP64 instruction costs as much as dozens of FP32 ones on this
+// part), converted to FP64 once per component.
 template <typename real, int TJ>
 static __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, long natoms_all, int nB,
                                   const int4* __restrict__ triblk, const real* __restrict__ cg,
@@ -94,6 +95,7 @@ static __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, lo
     const int s = (ta + tbb - tj) / 2;
     double B = 0.0;
     if constexpr (sizeof(real) == 4) {
+        FF Bf{0.f, 0.f};
         for (int p = 0; p <= tj; ++p)
             for (int q = 0; q <= tj; ++q) {
                 float zr = 0.f, zi = 0.f;
@@ -109,8 +111,9 @@ static __global__ void k_snap_bispectrum(const cplx<real>* __restrict__ utot, lo
                     }
                 }
                 const cplx<real> u = Uj[p * (tj + 1) + q];
-                B += (double)(u.re * zr) + (double)(u.im * zi);
+                Bf = ff_add(Bf, ff_two_sum(u.re * zr, u.im * zi));
             }
+        B = (double)Bf.hi + (double)Bf.lo;
     } else {
         for (int p = 0; p <= tj; ++p)
             for (int q = 0; q <= tj; ++q) {
