@@ -240,18 +240,25 @@ def _collect(procs):
     return out
 
 
-def _parareal(P, W, dev, torch, Nh=300, window=300, ncell=5, T=1500.0):
+def _parareal(P, W, dev, torch, Nh=300, window=300, ncell=5, T=1500.0, strategy=2):
     """Adaptive parareal (Algorithm 2) on a 251-atom cell vs the same N intervals run one after
     the other with the fine propagator (the paper's sequential cost N C_f), on this GPU.  The N
     intervals are cut into windows of `window` intervals; window w draws its noise with seed + w
     on both sides (interval ids 0 .. window - 1), and each trajectory starts a window from its own
-    end state of the previous one."""
+    end state of the previous one.  strategy 2: Finnis-Sinclair coarse propagator (the correction
+    sweep on a thread-block cluster); strategy 1: SNAP-6 (2J = 2) coarse propagator, coefficients
+    fitted like the fine ones (the one-CTA sweep)."""
     pos, box = W.bcc_sia(ncell)
     n = pos.shape[1]
     beta = torch.as_tensor(W.fitted_beta(), device=dev)
     q0 = torch.as_tensor(W.displaced(pos, 0.05, W.rng(5, 1)), device=dev)
     v0 = torch.as_tensor(W.velocities(n, T, W.rng(5, 2)), device=dev)
-    eng = P.Engine(n, box, P.snap_params(precision=P.FP32_BULK), P.fs_params(precision=P.FP32_BULK), beta=beta)
+    if strategy == 1:
+        eng = P.Engine(n, box, P.snap_params(precision=P.FP32_BULK),
+                       coarse_snap=P.snap_params(twojmax=2, precision=P.FP32_BULK), beta=beta,
+                       coarse_beta=torch.as_tensor(W.fitted_beta(2), device=dev))
+    else:
+        eng = P.Engine(n, box, P.snap_params(precision=P.FP32_BULK), P.fs_params(precision=P.FP32_BULK), beta=beta)
     eng.reserve(window)
     L, dconv, dexpl = 1, 1e-3, 0.1
     nwin = Nh // window
@@ -321,9 +328,11 @@ def _parareal(P, W, dev, torch, Nh=300, window=300, ncell=5, T=1500.0):
                 torch.cuda.synchronize()
                 width_ms[w] = (time.perf_counter() - t0) * 1e3
     t_fine_batches = sum(k * width_ms[b - a] for st in logs for (a, b, k, _) in st.log()) / 1e3
-    return {"workload": "251-atom W+SIA (5^3 cells), SNAP 2J=8 fitted (FP32-bulk) fine, FS EAM (FP32-bulk) coarse, "
+    coarse = "SNAP-6 (2J=2) fitted (FP32-bulk) coarse (Strategy I)" if strategy == 1 else \
+        "FS EAM (FP32-bulk) coarse (Strategy II)"
+    return {"workload": "251-atom W+SIA (5^3 cells), SNAP 2J=8 fitted (FP32-bulk) fine, %s, "
                         "dt 1 fs, L=1, 1500 K, gamma 1/ps, schedule C0=C1=2, N=%d intervals in windows of %d"
-                        % (Nh, window),
+                        % (coarse, Nh, window),
             "delta_conv_A": dconv, "delta_expl_A": dexpl, "metric": "max per-atom displacement (A)",
             "wall_sequential_s": t_seq, "wall_parareal_s": t_par, "speedup": t_seq / t_par,
             "n_slab": int(sum((st.log()[-1][3] + 1) if st.log() else 0 for st in logs)), "iterations": int(k_sum),
@@ -617,6 +626,7 @@ def run_ours(args):
         out["parareal"] = _parareal(P, W, dev, torch)                              # one window of 300
         out["parareal_windows_100"] = _parareal(P, W, dev, torch, window=100)     # three windows of 100
         out["parareal_windows_1000"] = _parareal(P, W, dev, torch, Nh=1000, window=1000)   # one window of 1000
+        out["parareal_strategy1_windows_100"] = _parareal(P, W, dev, torch, window=100, strategy=1)
 
     # ---- matched force error FP32-bulk vs FP64 and the plain-FP64 form on the same workload
     s64 = P.Snap(P.snap_params(precision=P.FP64))
