@@ -5,24 +5,25 @@
 // The sweep is sequential in n; what a cluster adds is the atoms of each interval spread over K
 // SMs (the one-CTA sweep runs every FP64 integrator operation, the EAM pair passes and the error
 // sums of all atoms on one SM).  CTA r owns the atoms [r m, r m + m), m = ceil(n / K), and keeps
-// a full copy of the positions (FP64 rows and the wrapped FP32 copy) and of the embedding
-// derivatives F'(rho) in its own shared memory; the owner of an atom writes its new values into
-// every CTA's copy through distributed shared memory (plain stores), followed by a cluster
-// barrier.  The positions are double-buffered: a publication goes to the buffer nobody reads
-// until the barrier after it, so a CTA still in its force pass never sees a half-updated copy
-// // (F'(rho) needs no second buffer: a position barrier always separates two force evaluations).
-// Per interval of one step: the corrected state and the list staleness of the previous interval,
-// the F'(rho) of each of the two force evaluations, and the drifted positions -- four cluster
-// barriers.  Every decision (rebuilding the Verlet lists, stopping at
-// an explosion) is taken from values every CTA combines in the same order, so all CTAs take the
-// same branches and reach the same barriers.
+// a full copy of the wrapped FP32 positions (and, in FP64 mode, of the FP64 rows) and of the
+// embedding derivatives F'(rho) in its own shared memory; the owner of an atom writes its new
+// values into every CTA's copy through distributed shared memory (plain stores), followed by a
+// cluster barrier.  The positions are double-buffered: a publication goes to the buffer nobody
+// reads until the barrier after it, so a CTA still in its force pass never sees a half-updated
+// copy (F'(rho) needs no second buffer: a position barrier always separates two force
+// evaluations).  Per interval of one step: the corrected state, the error partial sums and the
+// list staleness of the previous interval, the F'(rho) of each of the two force evaluations, and
+// the drifted positions -- four cluster barriers.  Every decision (rebuilding the Verlet lists,
+// stopping at an explosion) is taken from values every CTA combines in the same order, so all
+// CTAs take the same branches and reach the same barriers.
 //
 // Each atom's arithmetic is that of the one-CTA coarse kernels: the same Verlet list (every pair
-// within max(d, c) + skin in index order, rebuilt for all atoms when any atom has moved more than
-// half the skin), the same split of the pair entries over S threads per atom, the same pair
-// terms and integrator steps -- so C(cur_n) equals, bit for bit, the C(prev_n) that
-// k_coarse_batch computes for the jumps.  Only the slab error's sum over atoms runs in another
-// order (per CTA, then over the CTAs in rank order).
+// within max(d, c) + skin, rebuilt for all atoms when any atom has moved more than half the skin),
+// split into the same S sub-lists by neighbour index, the same pair terms summed in the same order,
+// the same integrator steps -- so C(cur_n) equals, bit for bit, the C(prev_n) that k_coarse_batch
+// computes for the jumps.  Only the slab error's sum over atoms runs in another order (per CTA,
+// then over the CTAs in rank order).  The thread layout differs from the one-CTA kernels: W
+// workers per sub-list in the pair passes, and the FP64 integrator split by axis (see the kernel).
 #pragma once
 
 #include <cfloat>
@@ -48,8 +49,9 @@ struct alignas(4 * sizeof(real)) ScTerm {
 };
 
 struct SweepClusterShared {
-    double* qb0;           // [3][n] all positions (replicated, two buffers; named, not an array
-    double* qb1;           // indexed at run time, which would put the pointers in local memory)
+    double* qb0;           // [3][n] positions, two buffers (all atoms' in FP64 mode, the own atoms'
+    double* qb1;           // in FP32 mode; named, not an array indexed at run time, which would
+                           // put the pointers in local memory)
     float4* qfb0;          // [n] wrapped FP32 positions (replicated, two buffers)
     float4* qfb1;
     double* q;             // the current buffers
