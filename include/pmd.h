@@ -295,6 +295,10 @@ int parareal_jumps(pmd_engine* e, int count, const double* fine_out, const doubl
  *   displacement |q_i^cur - q_i^prev| (Angstrom) over the same range.  A non-finite state
  *   counts as delta = +inf.
  * delta_host, n_stop_host: host outputs; *n_stop_host = n_fin when the sweep completes.
+ * Execution: with the Finnis-Sinclair coarse potential and 64 <= natoms <= 512 the sweep runs on
+ * one thread-block cluster of min(8, ceil(natoms/32)) CTAs (the atoms of each interval spread
+ * over its SMs); otherwise on one CTA.  Either way coarse_out equals, bit for bit, what
+ * baoab_propagate_batch(COARSE) computes from the same states.
  * This call SYNCHRONISES the stream (its outputs decide the host's next step).
  * L = steps per interval; lp as in baoab_propagate_batch. */
 int parareal_correct(pmd_engine* e, int n_in, int n_fin, const double* jumps, const double* prev,
