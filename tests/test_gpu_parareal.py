@@ -226,3 +226,69 @@ def test_cluster_sweep_adaptive_parareal_matches_algorithm_2_251_atoms():
     g = N(cur)
     for k in range(Nint + 1):
         assert np.abs(g[k, :3] - ocur[k][0]).max() < 1e-8
+
+
+def _host_delta(cur, prev, k, metric):
+    """The sweep's error after interval k (states 0..k+1), from the definition in pmd.h."""
+    c, p = N(cur[:k + 2, :3]), N(prev[:k + 2, :3])
+    if metric == P.METRIC_MAXDISP:
+        return float(np.sqrt(((c - p) ** 2).sum(axis=1)).max())
+    num = sum(np.linalg.norm(c[m] - p[m]) for m in range(k + 2))
+    den = sum(np.linalg.norm(p[m]) for m in range(k + 2))
+    return num / den
+
+
+@pytest.mark.parametrize("system", ["129", "433"])
+@pytest.mark.parametrize("metric", [P.METRIC_MAXDISP, P.METRIC_REL])
+def test_cluster_sweep_error_and_explosion_test(system, metric):
+    """The cluster sweep's running error and explosion test (Algorithm 2, "N_final := n"): the
+    returned delta equals the error recomputed on the host from the output states; a threshold
+    between two intervals' errors stops the sweep at the first interval above it, with the states
+    before the stop those of the full sweep; a threshold equal to the device's own error after
+    interval k does not stop at k (the maximum metric compares squares with a precomputed
+    threshold: exact at the boundary); a non-finite jump stops the sweep at its interval with
+    delta = inf and no device error, and with delta_expl = inf the next intervals integrate the
+    non-finite state and the call fails with ENONFINITE."""
+    pos, box = _sweep_system(system)
+    n = pos.shape[1]
+    Nn = 6
+    eng = P.Engine(n, box, P.snap_params(), P.fs_params(precision=P.FP32_BULK))
+    lp = P.langevin(dt=2e-3, gamma=1.0, T=2000.0, seed=29)
+    cur0 = torch.zeros(Nn + 1, 6, n, dtype=torch.float64, device=dev())
+    cur0[0, :3] = T(W.displaced(pos, 0.05, W.rng(26, 1)))
+    cur0[0, 3:] = T(W.velocities(n, 2000.0, W.rng(26, 2)))
+    prev = cur0.clone()
+    prev[1:] = cur0[0]                       # the error grows with the distance from the start
+    g = W.rng(26, 3)
+    J = T(np.concatenate([g.normal(0.0, 0.01, (Nn, 3, n)), g.normal(0.0, 0.2, (Nn, 3, n))], axis=1))
+
+    def run(nfin, dexpl, jumps=J, check=True):
+        cur = cur0.clone()
+        cache = torch.zeros(Nn, 6, n, dtype=torch.float64, device=dev())
+        d, ns = eng.parareal_correct(0, nfin, jumps, prev, cur, cache, dexpl, metric, 1, lp)
+        if check:
+            eng.sync_status()
+        return cur, d, ns
+
+    def first_above(thr):
+        return next((k for k in range(Nn) if D[k] > thr), Nn)
+
+    full, dA, nsA = run(Nn, float("inf"))
+    assert nsA == Nn
+    D = [_host_delta(full, prev, k, metric) for k in range(Nn)]
+    assert abs(dA - D[-1]) <= 1e-12 * D[-1]
+    k1 = next(k for k in range(1, Nn) if D[k] > D[k - 1] * (1 + 1e-6))   # an interval whose error rises
+    stop = first_above(0.5 * (D[k1 - 1] + D[k1]))
+    cut, dB, nsB = run(Nn, 0.5 * (D[k1 - 1] + D[k1]))
+    assert nsB == stop <= k1 and abs(dB - D[stop]) <= 1e-12 * D[stop]
+    assert torch.equal(cut[:stop + 1], full[:stop + 1])
+    _, dk, _ = run(k1, float("inf"))            # the device's own error after interval k1 - 1
+    assert abs(dk - D[k1 - 1]) <= 1e-12 * D[k1 - 1]
+    _, dC, nsC = run(Nn, dk)
+    assert nsC != k1 - 1 and nsC == first_above(dk * (1 + 1e-12))
+    Jn = J.clone()
+    Jn[1, 0, n // 2] = float("nan")
+    _, d, ns = run(Nn, 1e9, Jn)                 # reported by delta = inf; nothing integrated it
+    assert ns == 1 and d == float("inf")
+    with pytest.raises(P.PmdError, match="ENONFINITE"):   # delta_expl = inf: the next intervals
+        run(Nn, float("inf"), Jn, check=False)             # integrate it, and the call reports that
