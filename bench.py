@@ -41,7 +41,7 @@ WORKLOAD3 = ("2001-atom W+SIA cell (10^3 cells), SNAP 2J=8 fitted, 32 intervals 
 # capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on (fingerprint of the persistent kernel's translation unit and of
 # the host code that builds its tables); reported as null otherwise.
-TRAFFIC = {"bytes_per_launch": 3.30e6 + 19.80e6, "csrc_sha256_16": "137303b9cfcbeff7"}
+TRAFFIC = {"bytes_per_launch": 3.30e6 + 19.80e6, "csrc_sha256_16": "e366a45a5738d27b"}
 # CPU-baseline samples of the oracle: (intervals or members, steps each) of config 2 and config 3,
 # on all host cores; the single-thread legs take one interval or member of the same sample (the
 # oracle's per-atom-step cost on one thread does not depend on how many members a call holds)

@@ -23,7 +23,8 @@ struct EamShared {
     float4* qf;                // [n] wrapped to [0, L)
     double* F;                 // [3][n]
     double* dF;                // [n]
-    unsigned short* nbl;       // Verlet list, EAM_LIST_CAP per atom, eam_pidx layout (nullptr: scan all atoms)
+    unsigned short* nbl;       // Verlet list, EAM_LIST_CAP slots per atom (EAM_LIST_CAP / S per sub-list),
+                               // eam_pidx layout (nullptr: scan all atoms)
     unsigned char* nbc;        // [S][n] lengths of the per-thread sub-lists (see eam_build_list)
     float4* qref;              // [n] wrapped positions at the last list build
     float4* pg;                // FP32 pair geometry (dx, dy, dz, r) of the density pass, EAM_PG_CAP per atom,
@@ -40,7 +41,7 @@ struct EamShared {
 // the list's history (a list kept from earlier positions holds extra, rejected entries) and as a
 // scan over all atoms: C(x) is the same bits in the sweep, which keeps its list across intervals,
 // and in the batch, which builds a fresh one.
-constexpr int EAM_LIST_CAP = 64;
+constexpr int EAM_LIST_CAP = 64;   // a sub-list longer than EAM_LIST_CAP / S sets ST_NEIGH (ENEIGH)
 constexpr float EAM_SKIN = 0.5f;
 
 // FP32 pairs within the screen radius kept from the density pass for the force pass: up to
