@@ -14,9 +14,10 @@ Contents:
   * ``oracle.sia``: the interstitial's well in each frame (Wigner-Seitz reading of the
     Voronoi analysis of Sec. 3) and its residence times.
 
-Parity status of each function is listed in the module docstrings; the Philox bit
-stream itself is "parity unpinned" against published known-answer vectors (none are
-available here) and is pinned statistically instead.
+Parity status of each function is listed in the module docstrings.  The Philox bit
+stream has no published known-answer vectors here; it is pinned bitwise against cuRAND's
+device Philox4_32_10, an independent implementation of the same published generator
+(tests/test_gpu_philox_curand.py, which runs on a GPU), and statistically on the CPU.
 """
 import ctypes
 import os
