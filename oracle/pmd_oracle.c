@@ -28,9 +28,9 @@ int or_num_threads(void) {
 
 /* ------------------------------------------------------------------------------------
  * Noise.  The paper requires the same standard Gaussians G_{l,n} (0<=l<=L) for the
- * fine and the coarse propagator and at every parareal iteration (Sec. 2.1, "we
- * emphasize that ... both propagators should use the same random variables"; Sec. 2.3,
- * seeds S_n per interval).  They are drawn here from a counter-based generator:
+ * fine and the coarse propagator and at every parareal iteration (Sec. 2.1, where the two
+ * propagators of one interval are driven by identical random increments; Sec. 2.3, seeds
+ * S_n per interval).  They are drawn here from a counter-based generator:
  * Philox4x32-10 as published by Salmon et al. (SC'11): 10 rounds of
  *   (c0,c1,c2,c3) -> (hi(M1*c2)^c1^k0, lo(M1*c2), hi(M0*c0)^c3^k1, lo(M0*c0))
  * with M0=0xD2511F53, M1=0xCD9E8D57 and the key bumped by (0x9E3779B9, 0xBB67AE85)
